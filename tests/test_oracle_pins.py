@@ -1,0 +1,379 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: expected values come from
+numpy's FFT (the direct sum on the FFT grid), continuous Fourier transforms of
+Gaussians and points, conjugate symmetry, the adjoint identity, finite
+differences, Appendix B's noise formula, scipy's bounded minimisers, and
+closed-form minima.  Each test names the passage it follows.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1703_02920_gb300 import synth as S
+
+FORMS = ["direct", "factored"]
+
+
+def _grid_uv(N, dx, dy, kx, ky):
+    return np.asarray(kx) / (N * dx), np.asarray(ky) / (N * dy)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_forward_on_fft_grid_equals_fft2(oracle_mod, form):
+    """Eq. (1) on the pixel grid at u = kx/(N dx), v = ky/(N dy) is a 2-D DFT:
+    V = exp(+2 pi i (kx + ky) c / N) * FFT2(B)[ky, kx], c = N/2 (the pixel
+    origin of the gradient kernel, Section 2.5).  dx != dy catches a swapped axis."""
+    N, dx, dy = 16, 3e-7, 5e-7
+    rng = np.random.default_rng(1)
+    B = rng.random((N, N))
+    kx = np.array([0, 1, 3, -2, 5, 7, -8, 4])
+    ky = np.array([0, 2, -1, 4, -7, 1, 3, -8])
+    u, v = _grid_uv(N, dx, dy, kx, ky)
+    V = oracle_mod.forward(N, dx, dy, u, v, B, form)
+    c = N // 2
+    expect = np.fft.fft2(B)[ky % N, kx % N] * np.exp(2j * np.pi * (kx + ky) * c / N)
+    assert np.max(np.abs(V - expect)) <= 1e-13 * np.max(np.abs(expect))
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_adjoint_on_fft_grid_equals_ifft2(oracle_mod, form):
+    """Eq. (chi2gradient)'s sum Re(sum_k y_k exp(+2 pi i U_k.X)) on grid points is
+    N^2 * IFFT2 of the gridded, phase-shifted y."""
+    N, dx, dy = 16, 4e-7, 2e-7
+    rng = np.random.default_rng(2)
+    Z = 40
+    kx = rng.integers(-N // 2, N // 2, Z)
+    ky = rng.integers(-N // 2, N // 2, Z)
+    u, v = _grid_uv(N, dx, dy, kx, ky)
+    y = rng.standard_normal(Z) + 1j * rng.standard_normal(Z)
+    c = N // 2
+    Yg = np.zeros((N, N), dtype=complex)
+    np.add.at(Yg, (ky % N, kx % N), y * np.exp(-2j * np.pi * (kx + ky) * c / N))
+    expect = np.real(N * N * np.fft.ifft2(Yg))
+    if form == "factored":
+        G = oracle_mod.adjoint(N, dx, dy, u, v, y)
+    else:
+        G = oracle_mod.adjoint(N, dx, dy, u, v, y, crop=(0, N, 0, N), form="direct")
+    assert np.max(np.abs(G - expect)) <= 1e-12 * np.max(np.abs(expect))
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_point_source_at_phase_centre(oracle_mod, form):
+    """A point source of flux f at the phase centre gives V = f * A(0) for every (u,v)."""
+    N, dx = 32, S.ARCSEC * 0.1
+    rng = np.random.default_rng(3)
+    Z = 64
+    u = rng.uniform(-0.45, 0.45, Z) / dx
+    v = rng.uniform(-0.45, 0.45, Z) / dx
+    A = S.gaussian_beam(N, dx, dx, 20 * dx).astype(np.float64)
+    I = np.zeros((N, N))
+    I[N // 2, N // 2] = 0.37
+    V = oracle_mod.forward(N, dx, dx, u, v, A * I, form)
+    assert A[N // 2, N // 2] == 1.0
+    assert np.max(np.abs(V - 0.37)) <= 1e-14
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_offset_point_source_phase_ramp(oracle_mod, form):
+    """A point at pixel (n0, m0) gives the phase ramp f A exp(-2 pi i (u x0 + v y0))
+    with x0 = (m0 - N/2) dx, y0 = (n0 - N/2) dy (asymmetric in x/y)."""
+    N, dx, dy = 32, S.ARCSEC * 0.1, S.ARCSEC * 0.15
+    rng = np.random.default_rng(4)
+    Z = 64
+    u = rng.uniform(-0.45, 0.45, Z) / dx
+    v = rng.uniform(-0.45, 0.45, Z) / dy
+    A = S.gaussian_beam(N, dx, dy, 20 * dx).astype(np.float64)
+    n0, m0, f = 5, 23, 0.8
+    I = np.zeros((N, N))
+    I[n0, m0] = f
+    x0, y0 = (m0 - N // 2) * dx, (n0 - N // 2) * dy
+    V = oracle_mod.forward(N, dx, dy, u, v, A * I, form)
+    expect = f * A[n0, m0] * np.exp(-2j * np.pi * (u * x0 + v * y0))
+    assert np.max(np.abs(V - expect)) <= 1e-13
+
+
+def test_gaussian_times_beam_closed_form(oracle_mod):
+    """A well-sampled elliptical Gaussian times a Gaussian beam: the pixel sum
+    equals the continuous transform (Poisson summation; aliases and edge
+    truncation below 1e-10 for these widths)."""
+    N, dx = 96, S.ARCSEC * 0.1
+    comps = [S.Gaussian(flux=0.6, x0=0.3 * S.ARCSEC, y0=-0.2 * S.ARCSEC,
+                        fwhm_maj=1.0 * S.ARCSEC, fwhm_min=0.8 * S.ARCSEC, pa=0.6)]
+    beam = 6.0 * S.ARCSEC
+    rng = np.random.default_rng(5)
+    Z = 80
+    u = rng.uniform(-0.3, 0.3, Z) / dx
+    v = rng.uniform(-0.3, 0.3, Z) / dx
+    img = S.sky_image(comps, N, dx, dx)
+    x = (np.arange(N) - N // 2) * dx
+    A = np.exp(-0.5 * (x[:, None] ** 2 + x[None, :] ** 2) / (beam * S.FWHM_TO_SIGMA) ** 2)
+    V = oracle_mod.forward(N, dx, dx, u, v, A * img, "factored")
+    expect = S.sky_visibilities(comps, u, v, beam)
+    assert np.max(np.abs(V - expect)) <= 1e-10 * np.max(np.abs(expect))
+
+
+def test_circular_gaussian_textbook_transform(oracle_mod):
+    """Circular Gaussian of peak I0 (Jy/pixel) at the centre times a circular
+    Gaussian beam: V(u,v) = I0 * 2 pi s_e^2 / (dx dy) * exp(-2 pi^2 s_e^2 (u^2+v^2)),
+    s_e^2 = s_s^2 s_b^2 / (s_s^2 + s_b^2)."""
+    N, dx = 128, S.ARCSEC * 0.05
+    ss, sb = 4.0 * dx, 10.0 * dx
+    x = (np.arange(N) - N // 2) * dx
+    r2 = x[:, None] ** 2 + x[None, :] ** 2
+    I0 = 0.02
+    img = I0 * np.exp(-0.5 * r2 / ss ** 2)
+    A = np.exp(-0.5 * r2 / sb ** 2)
+    rng = np.random.default_rng(6)
+    Z = 50
+    u = rng.uniform(-0.2, 0.2, Z) / dx
+    v = rng.uniform(-0.2, 0.2, Z) / dx
+    se2 = ss ** 2 * sb ** 2 / (ss ** 2 + sb ** 2)
+    expect = I0 * 2 * np.pi * se2 / (dx * dx) * np.exp(-2 * np.pi ** 2 * se2 * (u ** 2 + v ** 2))
+    V = oracle_mod.forward(N, dx, dx, u, v, A * img, "factored")
+    assert np.max(np.abs(V - expect)) <= 1e-10 * expect.max()
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_hermitian_symmetry(oracle_mod, form):
+    """Real images have Hermitian visibilities: V(-u,-v) = conj V(u,v)."""
+    N, dx = 24, S.ARCSEC * 0.1
+    rng = np.random.default_rng(7)
+    B = rng.random((N, N))
+    u = rng.uniform(-0.45, 0.45, 30) / dx
+    v = rng.uniform(-0.45, 0.45, 30) / dx
+    V1 = oracle_mod.forward(N, dx, dx, u, v, B, form)
+    V2 = oracle_mod.forward(N, dx, dx, -u, -v, B, form)
+    assert np.max(np.abs(V2 - np.conj(V1))) <= 1e-13 * np.max(np.abs(V1))
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_adjoint_identity(oracle_mod, form):
+    """Re<F x, y> = <x, Re(F^H y)> for real x, complex y (Appendix C pairs the
+    model's derivative with the chi^2 gradient)."""
+    N, dx, dy = 20, S.ARCSEC * 0.1, S.ARCSEC * 0.12
+    rng = np.random.default_rng(8)
+    Z = 70
+    u = rng.uniform(-0.45, 0.45, Z) / dx
+    v = rng.uniform(-0.45, 0.45, Z) / dy
+    x = rng.standard_normal((N, N))
+    y = rng.standard_normal(Z) + 1j * rng.standard_normal(Z)
+    lhs = np.real(np.vdot(y, oracle_mod.forward(N, dx, dy, u, v, x, form)))
+    G = oracle_mod.adjoint(N, dx, dy, u, v, y, crop=(0, N, 0, N), form=form)
+    rhs = float(np.sum(x * G))
+    assert abs(lhs - rhs) <= 1e-12 * (np.sum(np.abs(x)) * np.sum(np.abs(y)))
+
+
+def test_factored_and_direct_agree(oracle_mod):
+    """The factored evaluation order reproduces the direct sum to rounding."""
+    N, dx, dy = 32, S.ARCSEC * 0.1, S.ARCSEC * 0.07
+    rng = np.random.default_rng(9)
+    Z = 100
+    u = rng.uniform(-0.45, 0.45, Z) / dx * 3  # several turns across the field
+    v = rng.uniform(-0.45, 0.45, Z) / dy * 3
+    B = rng.random((N, N))
+    y = rng.standard_normal(Z) + 1j * rng.standard_normal(Z)
+    Vd = oracle_mod.forward(N, dx, dy, u, v, B, "direct")
+    Vf = oracle_mod.forward(N, dx, dy, u, v, B, "factored")
+    assert np.max(np.abs(Vd - Vf)) <= 1e-12 * np.max(np.abs(Vd))
+    Gd = oracle_mod.adjoint(N, dx, dy, u, v, y, crop=(0, N, 0, N), form="direct")
+    Gf = oracle_mod.adjoint(N, dx, dy, u, v, y)
+    Gc = oracle_mod.adjoint(N, dx, dy, u, v, y, crop=(3, 10, 7, 12), form="factored")
+    assert np.max(np.abs(Gd - Gf)) <= 1e-12 * np.max(np.abs(Gd))
+    assert np.max(np.abs(Gc - Gd[3:13, 7:19])) <= 1e-12 * np.max(np.abs(Gd))
+
+
+def _tiny_problem(seed=10, N=8, Z=50, C=1, shared=False, lam=2.0):
+    ds = S.random_problem(N, Z, seed, C=C, shared_image=shared, lam=lam, G=1e-3)
+    return ds
+
+
+def test_chi2_gradient_central_differences_exact(oracle_mod):
+    """chi^2 is quadratic in I, so central differences are exact for any step
+    (Eq. phi2): [chi2(I + h e_p) - chi2(I - h e_p)] / 2h = d chi2 / d I_p."""
+    ds = _tiny_problem()
+    P = oracle_mod.Problem.from_dataset(ds, lam=0.0)
+    I = ds.truth.astype(np.float64)
+    _, _, _, g = oracle_mod.objective_grad(P, I)
+    rng = np.random.default_rng(11)
+    for p in rng.choice(P.N * P.N, 12, replace=False):
+        h = 0.05
+        e = np.zeros_like(I).ravel()
+        e[p] = h
+        e = e.reshape(I.shape)
+        fp = oracle_mod.objective(P, I + e)[1]
+        fm = oracle_mod.objective(P, I - e)[1]
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - g.ravel()[p]) <= 1e-9 * max(1.0, abs(g.ravel()[p]))
+
+
+@pytest.mark.parametrize("C,shared", [(1, False), (2, True), (3, False)])
+def test_objective_gradient_finite_differences(oracle_mod, C, shared):
+    """grad Phi = A Re(F^H w r) + lambda (1 + log(I/G)) against central differences
+    of Phi (Eq. phi3, Eq. Sgradient, Eq. chi2-multi for the shared image)."""
+    ds = _tiny_problem(seed=12 + C, C=C, shared=shared)
+    P = oracle_mod.Problem.from_dataset(ds)
+    I = ds.truth.astype(np.float64) + 0.01
+    phi, _, _, g = oracle_mod.objective_grad(P, I)
+    rng = np.random.default_rng(13)
+    for p in rng.choice(I.size, 10, replace=False):
+        h = 1e-6
+        e = np.zeros(I.size)
+        e[p] = h
+        e = e.reshape(I.shape)
+        fd = (oracle_mod.objective(P, I + e)[0] - oracle_mod.objective(P, I - e)[0]) / (2 * h)
+        assert abs(fd - g.ravel()[p]) <= 1e-6 * max(1.0, np.max(np.abs(g)))
+
+
+def test_zero_gradient_at_exact_data(oracle_mod):
+    """With V^o = F(A I) the chi^2 residuals vanish and so does grad chi^2; at
+    I = 0 the gradient is -A Re(F^H(w V^o)) (a weighted dirty image, Appendix A)."""
+    ds = _tiny_problem(seed=20)
+    P = oracle_mod.Problem.from_dataset(ds, lam=0.0)
+    I = ds.truth.astype(np.float64)
+    P.vo = oracle_mod.model_vis(P, I)[0]
+    phi, chi, _, g = oracle_mod.objective_grad(P, np.maximum(I, 1e-300))
+    assert chi <= 1e-25 and np.max(np.abs(g)) <= 1e-10
+    P2 = oracle_mod.Problem.from_dataset(ds, lam=0.0)
+    chis, res = oracle_mod.chi2_terms(P2, np.zeros_like(I))
+    g0 = oracle_mod.grad_chi2(P2, res)
+    w = 1.0 / ds.sigma ** 2
+    dirty = oracle_mod.adjoint(P2.N, P2.dx, P2.dy, ds.u, ds.v, w * ds.vo)
+    assert np.max(np.abs(g0[0] + ds.pb[0] * dirty)) <= 1e-12 * np.max(np.abs(g0))
+
+
+def test_entropy_maximal_at_prior_on_feasible_set(oracle_mod):
+    """S = -sum I log(I/G): stationary at I = G/e (dS/dI = -(1 + log(I/G))),
+    decreasing for I > G/e, so on I >= G it is largest at I = G (Eq. minproblem)."""
+    G = 1e-3
+    rng = np.random.default_rng(14)
+    s_prior = oracle_mod.entropy(np.full(64, G), G)
+    assert s_prior == 0.0
+    for _ in range(20):
+        I = G + rng.random(64) * rng.choice([1e-4, 1e-2, 1.0])
+        assert oracle_mod.entropy(I, G) < s_prior
+    # stationary point of the unconstrained entropy
+    h = 1e-9
+    s = lambda t: oracle_mod.entropy(np.array([t]), G)
+    d = (s(G / math.e + h) - s(G / math.e - h)) / (2 * h)
+    assert abs(d) < 1e-6
+    assert s(G / math.e) > s(G / math.e * 1.01) and s(G / math.e) > s(G / math.e * 0.99)
+
+
+def test_thermal_noise_appendix_b(oracle_mod):
+    """Appendix B: a noise-only natural-weight dirty pixel has standard deviation
+    sigma_D = (sum 1/sigma^2)^(-1/2), whatever the (u,v) coverage."""
+    N, dx = 8, S.ARCSEC * 0.1
+    rng = np.random.default_rng(15)
+    Z = 40
+    u = rng.uniform(-0.45, 0.45, Z) / dx
+    v = rng.uniform(-0.45, 0.45, Z) / dx
+    sigma = rng.uniform(0.5, 2.0, Z)
+    w = 1.0 / sigma ** 2
+    omega = w / w.sum()
+    vals = []
+    for s in range(1500):
+        r = np.random.default_rng(1000 + s)
+        noise = sigma * (r.standard_normal(Z) + 1j * r.standard_normal(Z))
+        vals.append(oracle_mod.adjoint(N, dx, dx, u, v, omega * noise, crop=(2, 1, 5, 1))[0, 0])
+    sd = np.std(vals)
+    assert abs(sd / oracle_mod.thermal_noise(sigma) - 1.0) < 0.08
+
+
+def test_generator_visibilities_match_pixel_sum(oracle_mod):
+    """The generator's closed-form visibilities of well-sampled Gaussians and
+    pixel-centred points equal the oracle's pixel sum of its pixelised sky."""
+    N, dx = 128, S.ARCSEC * 0.1
+    comps = [S.Gaussian(0.5, 0.5 * S.ARCSEC, 0.3 * S.ARCSEC, 1.5 * S.ARCSEC, 1.2 * S.ARCSEC, 1.1),
+             S.Gaussian(0.3, -1.0 * S.ARCSEC, 0.2 * S.ARCSEC, 1.2 * S.ARCSEC, 1.0 * S.ARCSEC, 0.2),
+             S.Point(0.2, 0.4 * S.ARCSEC, -0.8 * S.ARCSEC)]
+    beam = 12 * S.ARCSEC
+    rng = np.random.default_rng(16)
+    u = rng.uniform(-0.3, 0.3, 60) / dx
+    v = rng.uniform(-0.3, 0.3, 60) / dx
+    A = S.gaussian_beam(N, dx, dx, beam).astype(np.float64)
+    x = (np.arange(N) - N // 2) * dx
+    A64 = np.exp(-0.5 * (x[:, None] ** 2 + x[None, :] ** 2) / (beam * S.FWHM_TO_SIGMA) ** 2)
+    V = oracle_mod.forward(N, dx, dx, u, v, A64 * S.sky_image(comps, N, dx, dx))
+    expect = S.sky_visibilities(comps, u, v, beam)
+    assert np.max(np.abs(V - expect)) <= 1e-9 * np.max(np.abs(expect))
+    assert np.max(np.abs(A - A64)) < 1e-7
+
+
+def test_brent_matches_scipy_bounded_minimiser(oracle_mod):
+    """The line-search core (Brent 1973) finds the same minimiser as scipy's
+    bounded Brent on smooth unimodal functions."""
+    from scipy.optimize import minimize_scalar
+    fns = [lambda t: (t - 0.7) ** 2 + 0.1 * t ** 4,
+           lambda t: math.exp(t) - 3 * t,
+           lambda t: t * math.log(t) if t > 0 else 0.0]
+    for f in fns:
+        x, fx, n = oracle_mod.brent_min(f, 1e-3, 3.0, 1.0, f(1.0), 1e-8, 1e-12, 200)
+        ref = minimize_scalar(f, bounds=(1e-3, 3.0), method="bounded", options=dict(xatol=1e-10))
+        assert abs(x - ref.x) < 1e-6 and fx <= ref.fun + 1e-12
+
+
+def test_line_search_brackets_and_converges(oracle_mod):
+    """Bracketing by shrinking or golden expansion, then Brent: the accepted
+    step is within the tolerance of the true minimiser, from either side."""
+    for a_true, a0 in [(3.0, 0.1), (0.01, 5.0), (1.0, 1.0)]:
+        f = lambda t, a=a_true: (t - a) ** 2 / a + 1.0
+        alpha, fa, n = oracle_mod.line_search(f, f(0.0), a0)
+        assert abs(alpha - a_true) <= 5e-3 * a_true
+        assert n <= oracle_mod.LS_MAX_EVALS
+    alpha, fa, n = oracle_mod.line_search(lambda t: 1.0 + t, 1.0, 1.0)
+    assert alpha == 0.0
+
+
+def test_projection_rules(oracle_mod):
+    """Projected gradient and direction at the bound I = G (Eq. minproblem)."""
+    G = 1e-3
+    I = np.array([G, G, 2 * G, 3 * G])
+    g = np.array([1.0, -1.0, 1.0, -1.0])
+    assert np.array_equal(oracle_mod.project_grad(I, g, G), [0.0, -1.0, 1.0, -1.0])
+    d = np.array([-1.0, 1.0, -1.0, 1.0])
+    assert np.array_equal(oracle_mod.project_dir(I, d, G), [0.0, 1.0, -1.0, 1.0])
+
+
+def test_solver_reaches_bounded_minimiser(oracle_mod):
+    """For lambda > 0 Phi is strictly convex on I >= G (quadratic chi^2 plus
+    I log I), so the minimiser is unique: the projected CG lands on the point
+    scipy's L-BFGS-B finds with the same bounds, Phi never increases and every
+    iterate stays feasible."""
+    from scipy.optimize import minimize
+    ds = _tiny_problem(seed=21, N=8, Z=60, lam=50.0)
+    P = oracle_mod.Problem.from_dataset(ds)
+    I0 = np.full((1, 8, 8), P.G)
+    img, hists = oracle_mod.solve(P, I0, 150)
+    phis = [h["phi"] for h in hists[0]]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(phis, phis[1:]))
+    assert img.min() >= P.G
+
+    def fg(x):
+        phi, _, _, g = oracle_mod.objective_grad(P, x.reshape(1, 8, 8))
+        return phi, g.ravel()
+
+    ref = minimize(fg, np.full(64, 2 * P.G), jac=True, method="L-BFGS-B",
+                   bounds=[(P.G, None)] * 64, options=dict(maxiter=5000, ftol=1e-15, gtol=1e-12))
+    rel = np.linalg.norm(img.ravel() - ref.x) / np.linalg.norm(ref.x)
+    assert rel < 1e-3, rel
+    _, _, _, g = oracle_mod.objective_grad(P, img)
+    k_end = oracle_mod.kkt_residual(img, g, P.G)
+    _, _, _, g0 = oracle_mod.objective_grad(P, np.maximum(I0, P.G))
+    assert k_end < 1e-3 * oracle_mod.kkt_residual(np.maximum(I0, P.G), g0, P.G)
+
+
+def test_cube_mode_solves_channels_independently(oracle_mod):
+    """Cube mode: each channel is its own problem, so solving the cube equals
+    solving each channel alone."""
+    ds = _tiny_problem(seed=22, C=2, N=8, Z=40, lam=20.0)
+    P = oracle_mod.Problem.from_dataset(ds)
+    I0 = np.full((2, 8, 8), P.G)
+    imgs, _ = oracle_mod.solve(P, I0, 10)
+    for c in range(2):
+        s = P.sl(c)
+        Pc = oracle_mod.Problem(P.N, P.dx, P.dy, P.u[s], P.v[s], P.vo[s], P.sigma[s], P.pb[c:c + 1],
+                                np.array([0, s.stop - s.start]), P.G, P.lam)
+        ic, _ = oracle_mod.solve(Pc, I0[c:c + 1], 10)
+        assert np.array_equal(ic[0], imgs[c])
