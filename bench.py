@@ -1,0 +1,302 @@
+"""Benchmark: chi^2 + gradient evaluations of non-gridding MEM on one GB300.
+
+One step = one mem_objective_grad call over the whole data set: attenuation
+and operand preparation, forward operator with fused residual / chi^2,
+adjoint (chi^2 gradient), entropy, gradient assembly and projection.  The
+metric is vis*pixel/s = Z * N^2 * steps / s.  Default workload: the
+256 x 256, 999,600-visibility single-channel data set (50 antennas, 1 km
+disk, 816 Earth-rotation dumps), split-BF16 tensor-core form.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config 1..5] [--precision bf16x3|fp32_direct|fp64_direct]
+
+--impl reference times the FP64 CPU oracle on this machine's host cores on a
+bounded sample of the same workload (the paper's method as plainly stated).
+Multi-GPU: replicas only (each rank evaluates its own copy of the workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "chi2+gradient evals/s as vis*pixel/s"
+UNIT = "vis*pixel/s"
+WORKLOADS = {
+    1: "64x64 image, 10,260 vis (20 ant, 300 m, 27 dumps + conjugates)",
+    2: "256x256 image, 999,600 vis (50 ant, 1 km, 816 dumps)",
+    3: "512x512 image, 10,000,900 vis (50 ant, 2 km, 8,164 dumps)",
+    5: "1024x1024 image, 19,998,720 vis (64 ant, 3 km, 9,920 dumps)",
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_data(config: int):
+    from paper_1703_02920_gb300 import synth
+    return synth.make(config)
+
+
+def cpu_baseline(ds, budget_s: float = 12.0):
+    """FP64 oracle (as it stands) on a visibility subsample at full image size."""
+    import oracle
+    P = oracle.Problem.from_dataset(ds)
+    N = ds.N
+    img = np.maximum(ds.truth.astype(np.float64), ds.G)
+    z = 64
+    while True:
+        idx = np.linspace(0, ds.Z - 1, z).astype(np.int64)
+        sub = oracle.Problem(N, ds.dx, ds.dy, P.u[idx], P.v[idx], P.vo[idx], P.sigma[idx], P.pb[:1],
+                             np.array([0, z]), P.G, P.lam)
+        t0 = time.perf_counter()
+        oracle.objective_grad(sub, img[:1])
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or z >= ds.Z:
+            break
+        z = min(ds.Z, int(z * max(2.0, min(8.0, budget_s / 4 / max(dt, 1e-3)))))
+    evals = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.objective_grad(sub, img[:1])
+        evals += 1
+        if time.perf_counter() - t0 >= budget_s / 2:
+            break
+    dt = time.perf_counter() - t0
+    value = z * N * N * evals / dt
+    return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{evals} objective+gradient evaluation(s) on {z} of {ds.Z} visibilities "
+                      f"(evenly spaced) at full {N}x{N}, FP64 factored order, OpenMP"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    ds = make_data(args.config)
+    import oracle
+    oracle.build()
+    per = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        b = cpu_baseline(ds, budget_s=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
+        if k >= args.warmup:
+            per.append(b["value"])
+            info = b
+    value = statistics.mean(per)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "precision": "fp64 oracle (CPU)"},
+            "cpu_baseline": dict(info, value=value),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 5])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32_direct", "fp64_direct"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1703_02920_gb300 import memsynth
+
+    memsynth.load()
+    ds = make_data(args.config)
+    N, Z = ds.N, ds.Z
+    units = Z * N * N
+    ctx = memsynth.Context(ds, precision=args.precision)
+    stream = ctx.stream
+    img = torch.from_numpy(np.maximum(ds.truth, ds.G)).cuda()
+    grad = torch.empty_like(img)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    def step():
+        memsynth.mem_objective_grad(ctx.handle, img, grad, 0, want_scalars=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: CUDA events on the context stream per step, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launches()
+    ctx.profile(True)
+    ctx.profile_read()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = ctx.launches() - launches0
+    kprof = ctx.profile_read()
+    ctx.profile(False)
+    ctx.sync()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = sum(ms) / len(ms)
+    if dist is not None:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = units * world / (ms_step * 1e-3)
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    himg = torch.from_numpy(np.maximum(ds.truth, ds.G).astype(np.float32)).pin_memory().numpy()
+    hgrad = torch.empty(himg.shape, dtype=torch.float32).pin_memory().numpy()
+    for _ in range(2):
+        ctx.objective_grad_host(himg)
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        memsynth.mem_objective_grad_host(ctx.handle, himg, hgrad, 0)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_val = units * world / (statistics.mean(e2e_ms) * 1e-3)
+
+    # ---- roofline of the dominant kernel (algorithmic flops per launch / event time)
+    peaks, src = _peaks()
+    dom = max(kprof.items(), key=lambda kv: kv[1][0]) if kprof else ("none", (0.0, 1))
+    name, (tot_ms, cnt) = dom
+    avg_ms = tot_ms / max(cnt, 1)
+    # algorithmic work: 4 flops per (visibility, pixel) pair for each operator pass
+    flops = 4.0 * units
+    if name.startswith(("fwd", "adj")) and not name.endswith("reduce"):
+        achieved = flops / (avg_ms * 1e-3) / 1e12
+        if name.endswith("tc"):
+            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "note": f"{name}: {avg_ms:.3f} ms/launch, 4 algorithmic flops per vis*pixel "
+                            f"(12 executed in 3-term BF16: executed {3 * achieved:.0f} TFLOP/s); "
+                            f"peak = {src} sustained bf16"}
+        else:
+            roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
+                    "frac": None, "traffic": None, "note": f"{name}: {avg_ms:.3f} ms/launch"}
+    else:
+        roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": None, "traffic": None, "note": name}
+    kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1],
+                   "share": v[0] / max(sum(x[0] for x in kprof.values()), 1e-30)} for k, v in kprof.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(ds)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16x3" if args.precision == "bf16x3" else
+                ("f32" if args.precision == "fp32_direct" else "f64"),
+                "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.config], "precision": args.precision,
+                           "image": f"{N}x{N}", "visibilities": Z, "parallelism": f"replicas x{world}",
+                           "l2": "flushed between timed steps (256 MB write)"},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(img.numel() * 4),
+                        "d2h_bytes_per_step": int(img.numel() * 4 + 24)},
+                "gpu_launches": launches,
+                "roofline": roof, "kernels": kernels,
+                "clocks": clk.summary(), "cpu_baseline": cpu}
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

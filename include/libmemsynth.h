@@ -1,0 +1,185 @@
+/*
+ * libmemsynth — non-gridding maximum-entropy image synthesis on one GB300.
+ *
+ * C ABI of the hot path of Carcamo et al., "Multi-GPU maximum entropy image
+ * synthesis for radio astronomy" (arXiv:1703.02920): the measurement operator
+ * of Eq. (1) evaluated as a direct (non-gridded) sum at every (u,v) sample,
+ * its adjoint (the chi^2 gradient, Eq. chi2gradient / Appendix C), the entropy
+ * term and its gradient (Eq. logentropy, Eq. Sgradient), the positivity bound
+ * I >= G (Eq. minproblem) and the projected conjugate-gradient solve.
+ *
+ * Notation.  N = image side, pixels row-major [y][x] (index n*N + m) with
+ * pixel coordinates x_m = (m - N/2) dx, y_n = (n - N/2) dy (radians; the pixel
+ * origin of the gradient kernel in Section 2.5).  u, v in wavelengths.
+ * Visibilities are interleaved (re, im).  A is the primary beam (Section 2.4,
+ * step 1), B = A * I the attenuated image, w_k = 1 / sigma_k^2.
+ *
+ *   forward   V_k   = sum_{n,m} B[n][m] exp(-2 pi i (u_k x_m + v_k y_n))
+ *   adjoint   G[n][m] = A[n][m] * sum_k Re( y_k exp(+2 pi i (u_k x_m + v_k y_n)) )
+ *   chi^2     = 1/2 sum_k w_k |V_k - V^o_k|^2                      (Eq. phi2)
+ *   entropy   S = - sum_i I_i log(I_i / G)                          (Eq. logentropy;
+ *               the paper's (I/G) log(I/G) scale is folded into lambda)
+ *   objective Phi = chi^2 - lambda S                                (Eq. phi3)
+ *   gradient  grad Phi = A * Re(F^H (w r)) + lambda (1 + log(I/G)),  r = V - V^o
+ *
+ * Multi-channel data (Section 2.1, Eq. chi2-multi): visibilities of channel c
+ * are the index range [vis_offsets[c], vis_offsets[c+1]); channel c has its
+ * own primary beam A_c (C*N*N floats).  MEM_IMAGES_PER_CHANNEL treats each
+ * channel as an independent image (a line cube, C*N*N floats per image
+ * argument); MEM_IMAGE_SHARED fits one N*N image to all channels, chi^2
+ * summed over channels as in Eq. chi2-multi.
+ *
+ * Ownership and threading.  The caller owns every pointer it passes.
+ * mem_create copies the data into device memory owned by the context (the
+ * data stays resident, Section 2.5 "keep most of the data in global memory").
+ * Arguments named *_dev are device pointers the caller allocated (e.g. torch
+ * tensors); work is enqueued on the stream given to mem_create and calls
+ * returning scalars to the host synchronise that stream.  A context is used
+ * from one host thread at a time and is not re-entrant.
+ *
+ * Errors.  Every call returns a mem_status; nothing is thrown across the ABI.
+ * mem_last_error() gives a message for the last failing call of a context.
+ * Device-side waits are bounded (mem_config.spin_limit); a wait that runs out
+ * makes the call return MEM_ETIMEOUT without faulting the GPU.  A non-finite
+ * objective returns MEM_ENUMERIC.  There is no CPU fallback: without a usable
+ * sm_103a GPU, mem_create returns MEM_ECUDA.
+ */
+#ifndef LIBMEMSYNTH_H
+#define LIBMEMSYNTH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mem_ctx mem_ctx;
+
+typedef enum {
+    MEM_OK = 0,
+    MEM_EINVAL = 1,    /* bad argument (null pointer, size, unsupported combination) */
+    MEM_ENOMEM = 2,    /* device allocation failed or exceeded MEMSYNTH_MAX_BYTES */
+    MEM_ECUDA = 3,     /* CUDA runtime error, or no sm_103a device */
+    MEM_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
+    MEM_ENUMERIC = 5,  /* objective not finite */
+    MEM_ENOTSUP = 6    /* form not available */
+} mem_status;
+
+/* Number format of the operator pair.  Every form computes the same sums
+ * (Eq. 1 and Eq. chi2gradient); they differ in arithmetic.  Phase arguments
+ * u x + v y are always reduced exactly (64-bit fixed-point turns obtained
+ * from an FP64 reduction of u dx and v dy). */
+typedef enum {
+    MEM_PREC_FP64_DIRECT = 0,  /* one FP64 exponential per (visibility, pixel) pair */
+    MEM_PREC_FP32_DIRECT = 1,  /* one FP32 (SFU) exponential per pair, FP64 partial sums */
+    MEM_PREC_BF16X3 = 2        /* separable phase tables generated on chip, tcgen05
+                                  tensor-core contractions in 3-term split BF16 with FP32
+                                  accumulation, FP64 cross-tile reductions */
+} mem_precision;
+
+typedef enum {
+    MEM_IMAGES_PER_CHANNEL = 0,
+    MEM_IMAGE_SHARED = 1
+} mem_image_mode;
+
+typedef struct {
+    int32_t n;                   /* image side N, 16 <= N <= 4096, multiple of 16 */
+    double dx, dy;               /* pixel size in radians, > 0 */
+    int32_t n_channels;          /* C >= 1 */
+    const int64_t *vis_offsets;  /* host, C+1 non-decreasing entries, [0] = 0, [C] = Z total */
+    double lambda;               /* entropy weight (>= 0) in Phi = chi^2 + lambda sum I log(I/G) */
+    double G;                    /* lower bound and entropy reference, > 0 (Jy/pixel) */
+    int32_t precision;           /* mem_precision */
+    int32_t image_mode;          /* mem_image_mode */
+    uint64_t spin_limit;         /* bound on device-side wait iterations; 0 = default (2^26) */
+} mem_config;
+
+/* Per-call summary of mem_solve. */
+typedef struct {
+    int32_t iterations;    /* CG iterations completed (per image, max over images) */
+    int32_t evaluations;   /* objective evaluations (forward passes), summed over images */
+    int32_t status;        /* mem_status of the solve */
+    int32_t stopped_early; /* 1 if an image stopped before n_iter (no descent / no decrease) */
+    double phi, chi2, entropy;  /* final values summed over images */
+} mem_solve_report;
+
+/* Create a context: validates cfg, copies u, v (Z doubles each), vis_obs (2Z
+ * doubles, interleaved re/im), sigma (Z doubles, > 0) and pb (C*N*N floats)
+ * to the device, prepares per-visibility phase increments (FP64 reduction of
+ * u dx, v dy to 64-bit fixed-point turns) and binds the context to `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  All host pointers. */
+mem_status mem_create(const mem_config *cfg, const double *u, const double *v,
+                      const double *vis_obs, const double *sigma, const float *pb,
+                      void *stream, mem_ctx **out);
+
+void mem_destroy(mem_ctx *ctx);
+
+/* Message for the last failing call on ctx (or a global one when ctx is NULL). */
+const char *mem_last_error(const mem_ctx *ctx);
+const char *mem_status_string(mem_status s);
+
+/* Switch the number format used by later calls (same data, no re-upload). */
+mem_status mem_set_precision(mem_ctx *ctx, int32_t precision);
+
+/* Sizes: total visibilities, channels, images (C or 1), image side. */
+int64_t mem_num_vis(const mem_ctx *ctx);
+int32_t mem_num_images(const mem_ctx *ctx);
+
+/* Forward operator, Eq. (1): vis_dev[2k], vis_dev[2k+1] = Re, Im of
+ * V_k = F_c(A_c * I_c) for k in channel c.  image_dev: C*N*N floats (cube)
+ * or N*N (shared).  vis_dev: 2*Z floats. */
+mem_status mem_forward(mem_ctx *ctx, const float *image_dev, float *vis_dev);
+
+/* Adjoint, Eq. (chi2gradient) with the beam factor: img_dev = A_c *
+ * Re(F_c^H y_c) per channel image (cube) or summed over channels (shared).
+ * y_dev: 2*Z floats (re, im).  img_dev: C*N*N or N*N floats. */
+mem_status mem_adjoint(mem_ctx *ctx, const float *y_dev, float *img_dev);
+
+/* Objective and gradient at image_dev (all pixels must be > 0): writes
+ * grad_dev (same shape as the image; NULL to skip) with grad Phi, or the
+ * positively projected gradient when `projected` != 0 (components with
+ * I <= G and grad > 0 set to 0).  out3_host (nullable) receives Phi, chi^2, S
+ * summed over images; passing it synchronises the stream.  The last values
+ * also stay on the device, see mem_scalars_dev. */
+mem_status mem_objective_grad(mem_ctx *ctx, const float *image_dev, float *grad_dev,
+                              int32_t projected, double *out3_host);
+
+/* Same as mem_objective_grad with host buffers: copies image_host to the
+ * device and grad_host back within the call (synchronous). */
+mem_status mem_objective_grad_host(mem_ctx *ctx, const float *image_host, float *grad_host,
+                                   int32_t projected, double *out3_host);
+
+/* Device pointer to 3 doubles (Phi, chi^2, S) of the last objective call. */
+const double *mem_scalars_dev(const mem_ctx *ctx);
+
+/* Minimise Phi over I >= G (Eq. minproblem) from image_dev_inout (clipped to
+ * G first), n_iter projected Polak-Ribiere CG iterations per image, each with
+ * a bracketing + Brent line search.  Cube mode runs one independent CG per
+ * channel image, all channels batched in every launch.  hist_host (nullable,
+ * host) receives per image and iteration 0..n_iter the 6 doubles (Phi, chi^2,
+ * S, alpha, beta, evaluations), laid out [image][iteration][6]; iterations
+ * after an early stop repeat the last values. */
+mem_status mem_solve(mem_ctx *ctx, float *image_dev_inout, int32_t n_iter,
+                     mem_solve_report *rep, double *hist_host);
+
+/* Wait for all work of ctx; returns MEM_ETIMEOUT / MEM_ECUDA if a kernel
+ * reported a bounded-wait timeout or a CUDA error occurred. */
+mem_status mem_sync(mem_ctx *ctx);
+
+/* Kernel launches issued by ctx since creation (for launch accounting). */
+int64_t mem_launch_count(const mem_ctx *ctx);
+
+/* Per-kernel timing for measurement: when enabled, every kernel launch of ctx
+ * is bracketed by CUDA events recorded on the context stream.
+ * mem_profile_read synchronises the stream, writes up to max_kernels entries
+ * (names: 32 chars each, NUL-terminated; total milliseconds; launch counts),
+ * clears the accumulators and returns the number of entries (-1 on error). */
+mem_status mem_profile(mem_ctx *ctx, int32_t enable);
+int32_t mem_profile_read(mem_ctx *ctx, int32_t max_kernels, char *names, double *ms_total,
+                         int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBMEMSYNTH_H */

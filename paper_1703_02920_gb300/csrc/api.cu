@@ -1,0 +1,1059 @@
+// libmemsynth C ABI: context, buffers, work lists, launch sequences and the
+// projected conjugate-gradient driver.  Declarations and semantics:
+// include/libmemsynth.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/libmemsynth.h"
+#include "internal.h"
+
+using namespace msk;
+
+namespace {
+
+thread_local std::string g_last_error = "";
+
+// Projected Polak-Ribiere CG and line-search constants.  The paper names a
+// Numerical-Recipes style CG with bracketing and Brent line minimisation
+// (Section 4.2) without giving constants; these are this library's reading.
+constexpr double GOLD = 1.618033988749895;    // bracket expansion ratio
+constexpr double CGOLD = 0.3819660112501051;  // golden-section fraction
+constexpr double SHRINK = 0.25;               // trial-step reduction
+constexpr int LS_MAX_EVALS = 20;              // objective evaluations per line search
+constexpr double LS_TOL = 1e-3;               // relative step tolerance (Brent)
+constexpr double LS_EPS = 1e-10;              // absolute tolerance / first trial step
+constexpr int RESTART = 50;                   // steepest-descent restart period
+
+// Line search on phi(alpha), alpha >= 0, as a resumable state machine so that
+// many images (cube channels) can share each batched objective evaluation.
+// Bracketing: shrink the trial step until phi < phi(0), or expand it by GOLD
+// while phi keeps falling; then Brent's method (Brent 1973, ch. 5).
+struct LineSearch {
+    enum Phase { INIT, SHRINK_P, EXPAND, BRENT, DONE } phase = DONE;
+    int evals = 0, nb = 0, budget = 0;
+    double f0 = 0, a = 0, fa = 0, b = 0, fb = 0, c = 0, fc = 0, eps = 0;
+    double lo = 0, hi = 0, x = 0, w = 0, v = 0, fx = 0, fw = 0, fv = 0, d = 0, e = 0;
+    double req = 0, alpha = 0, falpha = 0;
+
+    void start(double phi0, double alpha0) {
+        f0 = phi0;
+        eps = LS_EPS * alpha0;
+        a = 0.0;
+        fa = phi0;
+        b = alpha0;
+        req = b;
+        evals = 0;
+        phase = INIT;
+    }
+    bool running() const { return phase != DONE; }
+    void finish(double al, double f) {
+        alpha = al;
+        falpha = f;
+        phase = DONE;
+    }
+    void shrink_check() {
+        if (fb >= fa && evals < LS_MAX_EVALS) {
+            c = b;
+            fc = fb;
+            b = b * SHRINK;
+            req = b;
+            phase = SHRINK_P;
+        } else if (fb >= fa) {
+            finish(0.0, f0);
+        } else {
+            brent_start();
+        }
+    }
+    void expand_check() {
+        if (fc < fb && evals < LS_MAX_EVALS) {
+            a = b;
+            fa = fb;
+            b = c;
+            fb = fc;
+            c = b + GOLD * (b - a);
+            req = c;
+            phase = EXPAND;
+        } else if (fc < fb) {
+            finish(c, fc);
+        } else {
+            brent_start();
+        }
+    }
+    void brent_start() {
+        lo = a;
+        hi = c;
+        x = w = v = b;
+        fx = fw = fv = fb;
+        d = e = 0.0;
+        nb = 0;
+        budget = LS_MAX_EVALS - evals;
+        phase = BRENT;
+        brent_step();
+    }
+    void brent_step() {
+        if (nb >= budget) {
+            evals += nb;
+            finish(x, fx);
+            return;
+        }
+        const double xm = 0.5 * (lo + hi);
+        const double tol1 = LS_TOL * std::fabs(x) + eps;
+        const double tol2 = 2.0 * tol1;
+        if (std::fabs(x - xm) <= tol2 - 0.5 * (hi - lo)) {
+            evals += nb;
+            finish(x, fx);
+            return;
+        }
+        bool golden = true;
+        if (std::fabs(e) > tol1) {
+            double r = (x - w) * (fx - fv);
+            double q = (x - v) * (fx - fw);
+            double p = (x - v) * q - (x - w) * r;
+            q = 2.0 * (q - r);
+            if (q > 0.0) p = -p;
+            else q = -q;
+            const double e_prev = e;
+            e = d;
+            if (std::fabs(p) < std::fabs(0.5 * q * e_prev) && p > q * (lo - x) && p < q * (hi - x)) {
+                d = p / q;
+                const double t = x + d;
+                if ((t - lo) < tol2 || (hi - t) < tol2) d = (xm >= x) ? tol1 : -tol1;
+                golden = false;
+            }
+        }
+        if (golden) {
+            e = (x >= xm) ? (lo - x) : (hi - x);
+            d = CGOLD * e;
+        }
+        req = (std::fabs(d) >= tol1) ? x + d : x + (d >= 0.0 ? tol1 : -tol1);
+    }
+    void feed(double f) {
+        switch (phase) {
+            case INIT:
+                fb = f;
+                evals = 1;
+                if (fb >= fa) {
+                    c = b;
+                    fc = fb;
+                    shrink_check();
+                } else {
+                    c = b + GOLD * (b - a);
+                    req = c;
+                    phase = EXPAND;
+                }
+                break;
+            case SHRINK_P:
+                fb = f;
+                evals += 1;
+                shrink_check();
+                break;
+            case EXPAND:
+                fc = f;
+                evals += 1;
+                expand_check();
+                break;
+            case BRENT: {
+                const double t = req, ft = f;
+                nb += 1;
+                if (ft <= fx) {
+                    if (t >= x) lo = x;
+                    else hi = x;
+                    v = w;
+                    fv = fw;
+                    w = x;
+                    fw = fx;
+                    x = t;
+                    fx = ft;
+                } else {
+                    if (t < x) lo = t;
+                    else hi = t;
+                    if (ft <= fw || w == x) {
+                        v = w;
+                        fv = fw;
+                        w = t;
+                        fw = ft;
+                    } else if (ft <= fv || v == x || v == w) {
+                        v = t;
+                        fv = ft;
+                    }
+                }
+                brent_step();
+                break;
+            }
+            case DONE:
+                break;
+        }
+    }
+};
+
+size_t alloc_cap() {
+    const char* s = std::getenv("MEMSYNTH_MAX_BYTES");
+    if (!s || !*s) return (size_t)-1;
+    return (size_t)std::strtoull(s, nullptr, 10);
+}
+
+}  // namespace
+
+struct mem_ctx {
+    // problem
+    int N = 0, C = 0, n_images = 0, shared = 0, prec = 0;
+    double dx = 0, dy = 0, lambda = 0, G = 0;
+    uint64_t spin = 0;
+    int64_t Z = 0;
+    std::vector<int64_t> off;
+    cudaStream_t st = nullptr;
+    int device = 0, num_sms = 0;
+    std::string err;
+    int64_t launches = 0;
+    size_t bytes = 0, cap = (size_t)-1;
+    std::vector<void*> allocs;
+
+    // resident data
+    double *u = nullptr, *v = nullptr, *w = nullptr;
+    uint64_t *pa = nullptr, *pb = nullptr;
+    double2* vo = nullptr;
+    float* beam = nullptr;
+    int64_t* doff = nullptr;
+
+    // work lists
+    std::vector<VisTile> tiles_h;
+    std::vector<int> tile_off_h;
+    VisTile* tiles = nullptr;
+    int* tile_off = nullptr;
+    int n_tiles = 0;
+    std::vector<AdjUnit> units_h;
+    std::vector<int> cta_off_h, cb_off_h;
+    AdjUnit* units = nullptr;
+    int *cta_off = nullptr, *cb_off = nullptr;
+    int adj_ctas = 0;
+
+    // scratch
+    float2* y32 = nullptr;
+    double2* y64 = nullptr;
+    double *chi_part = nullptr, *ent_part = nullptr, *gsum = nullptr, *scal = nullptr, *img_tmp = nullptr;
+    int gsum_ks = 0;
+    float* bf32 = nullptr;
+    double* bf64 = nullptr;
+    uint16_t* planes = nullptr;
+    float* partial = nullptr;
+    int* dstatus = nullptr;
+    float* stage = nullptr;  // host-call staging (image, gradient)
+
+    // optional per-kernel timing (CUDA events on the context stream)
+    bool profiling = false;
+    struct KEv {
+        const char* name;
+        cudaEvent_t a, b;
+    };
+    std::vector<KEv> kev;
+    std::vector<cudaEvent_t> ev_pool;
+    std::map<std::string, std::pair<double, int64_t>> kacc;
+
+    // solver state
+    double *I64 = nullptr, *d64 = nullptr, *g64 = nullptr, *gf64 = nullptr, *gp64 = nullptr;
+    double *alpha = nullptr, *beta = nullptr, *dots = nullptr, *dpart = nullptr;
+    int* mode = nullptr;
+
+    DevData dd() const {
+        DevData d;
+        d.N = N;
+        d.C = C;
+        d.n_images = n_images;
+        d.shared = shared;
+        d.G = G;
+        d.lambda = lambda;
+        d.pa = pa;
+        d.pb = pb;
+        d.u = u;
+        d.v = v;
+        d.vo = vo;
+        d.w = w;
+        d.beam = beam;
+        d.off = doff;
+        return d;
+    }
+};
+
+namespace {
+
+cudaEvent_t pool_event(mem_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one kernel launch with CUDA events when profiling is on.
+struct KTimer {
+    mem_ctx* c;
+    const char* name;
+    cudaEvent_t a = nullptr;
+    KTimer(mem_ctx* ctx, const char* n) : c(ctx), name(n) {
+        if (c->profiling) {
+            a = pool_event(c);
+            cudaEventRecord(a, c->st);
+        }
+    }
+    ~KTimer() {
+        if (a) {
+            cudaEvent_t b = pool_event(c);
+            cudaEventRecord(b, c->st);
+            c->kev.push_back({name, a, b});
+        }
+    }
+};
+
+mem_status fail(mem_ctx* c, mem_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    g_last_error = buf;
+    return s;
+}
+
+mem_status cuda_fail(mem_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, MEM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                        \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+template <typename T>
+mem_status dalloc(mem_ctx* c, T** p, size_t count) {
+    if (*p) return MEM_OK;
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    if (c->bytes + bytes > c->cap)
+        return fail(c, MEM_ENOMEM, "device allocation of %zu bytes exceeds MEMSYNTH_MAX_BYTES", bytes);
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, MEM_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    c->bytes += bytes;
+    c->allocs.push_back(q);
+    *p = (T*)q;
+    return MEM_OK;
+}
+
+#define TRY(x)                           \
+    do {                                 \
+        mem_status s_ = (x);             \
+        if (s_ != MEM_OK) return s_;     \
+    } while (0)
+
+bool tc_shape_ok(int N) { return N == 64 || N == 128 || (N >= 256 && N % 256 == 0); }
+
+// 128-visibility tiles per channel, in channel order.
+void build_tiles(mem_ctx* c) {
+    c->tiles_h.clear();
+    c->tile_off_h.assign(c->C + 1, 0);
+    for (int ch = 0; ch < c->C; ++ch) {
+        c->tile_off_h[ch] = (int)c->tiles_h.size();
+        for (int64_t s = c->off[ch]; s < c->off[ch + 1]; s += 128) {
+            VisTile t;
+            t.chan = ch;
+            t.start = s;
+            t.count = (int)std::min<int64_t>(128, c->off[ch + 1] - s);
+            c->tiles_h.push_back(t);
+        }
+    }
+    c->tile_off_h[c->C] = (int)c->tiles_h.size();
+    c->n_tiles = (int)c->tiles_h.size();
+}
+
+// Split-K work of the tensor-core adjoint: the (channel, output block)
+// segments' 16-visibility stages concatenated and cut into one contiguous run
+// per CTA; every (CTA, segment) overlap is a unit with its own partial.
+void build_units(mem_ctx* c) {
+    const int BLK = tca_blk(c->N), nbx = c->N / BLK, nb = nbx * nbx;
+    std::vector<int64_t> seg_st;  // stage count per segment (c, blk)
+    int64_t T = 0;
+    for (int ch = 0; ch < c->C; ++ch) {
+        int64_t z = c->off[ch + 1] - c->off[ch];
+        for (int b = 0; b < nb; ++b) {
+            int64_t s = (z + TCA_BK - 1) / TCA_BK;
+            seg_st.push_back(s);
+            T += s;
+        }
+    }
+    c->units_h.clear();
+    c->cta_off_h.clear();
+    c->cb_off_h.assign((size_t)c->C * nb + 1, 0);
+    int G = (int)std::min<int64_t>(c->num_sms, T);
+    c->adj_ctas = G;
+    if (G <= 0) {
+        c->cta_off_h.push_back(0);
+        return;
+    }
+    // CTA g takes global stages [T g / G, T (g+1) / G)
+    size_t seg = 0;
+    int64_t seg_base = 0;  // first global stage of segment `seg`
+    std::vector<int> cb_count((size_t)c->C * nb, 0);
+    for (int g = 0; g < G; ++g) {
+        c->cta_off_h.push_back((int)c->units_h.size());
+        int64_t s0 = T * g / G, s1 = T * (g + 1) / G;
+        while (s0 < s1) {
+            while (seg < seg_st.size() && seg_base + seg_st[seg] <= s0) {
+                seg_base += seg_st[seg];
+                ++seg;
+            }
+            int64_t e = std::min<int64_t>(s1, seg_base + seg_st[seg]);
+            int ch = (int)(seg / nb), b = (int)(seg % nb);
+            int64_t z0 = c->off[ch], z1 = c->off[ch + 1];
+            AdjUnit un;
+            un.chan = ch;
+            un.block = b;
+            un.start = z0 + (s0 - seg_base) * TCA_BK;
+            un.count = std::min<int64_t>(z1, z0 + (e - seg_base) * TCA_BK) - un.start;
+            c->units_h.push_back(un);
+            cb_count[seg] += 1;
+            s0 = e;
+        }
+    }
+    c->cta_off_h.push_back((int)c->units_h.size());
+    for (size_t i = 0; i < cb_count.size(); ++i) c->cb_off_h[i + 1] = c->cb_off_h[i] + cb_count[i];
+}
+
+mem_status check_status(mem_ctx* c) {
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st), "status readback");
+    CK(cudaStreamSynchronize(c->st), "stream synchronize");
+    if (hs & DEV_TIMEOUT) {
+        cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st);
+        cudaStreamSynchronize(c->st);
+        return fail(c, MEM_ETIMEOUT, "a bounded device-side wait ran out (spin_limit %llu)",
+                    (unsigned long long)c->spin);
+    }
+    return MEM_OK;
+}
+
+mem_status after_launch(mem_ctx* c, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    return MEM_OK;
+}
+
+// Buffers needed by the current precision.
+mem_status ensure_buffers(mem_ctx* c) {
+    const size_t NN = (size_t)c->N * c->N;
+    TRY(dalloc(c, &c->chi_part, (size_t)4 * std::max(c->n_tiles, 1)));
+    TRY(dalloc(c, &c->ent_part, (size_t)c->n_images * prep_blocks(c->N)));
+    TRY(dalloc(c, &c->scal, (size_t)3 + 3 * c->n_images));
+    TRY(dalloc(c, &c->img_tmp, (size_t)3 * c->n_images));
+    TRY(dalloc(c, &c->y32, (size_t)std::max<int64_t>(c->Z, 1)));
+    if (c->prec == MEM_PREC_FP64_DIRECT) {
+        TRY(dalloc(c, &c->y64, (size_t)std::max<int64_t>(c->Z, 1)));
+        TRY(dalloc(c, &c->bf64, (size_t)c->C * NN));
+    } else if (c->prec == MEM_PREC_FP32_DIRECT) {
+        TRY(dalloc(c, &c->bf32, (size_t)c->C * NN));
+    } else {
+        TRY(dalloc(c, &c->planes, (size_t)2 * c->C * NN));
+        const int BLK = tca_blk(c->N);
+        TRY(dalloc(c, &c->partial, std::max<size_t>(c->units_h.size(), 1) * BLK * BLK));
+    }
+    int ks = 1;
+    if (c->prec != MEM_PREC_BF16X3) ks = adj_direct_splits(c->dd(), c->num_sms);
+    if (ks > c->gsum_ks) {
+        // grow: the old block stays allocated until destroy (rare)
+        c->gsum = nullptr;
+        TRY(dalloc(c, &c->gsum, (size_t)ks * c->C * NN));
+        c->gsum_ks = ks;
+    }
+    return MEM_OK;
+}
+
+int bformat(int prec) {
+    return prec == MEM_PREC_FP64_DIRECT ? BF_F64 : prec == MEM_PREC_FP32_DIRECT ? BF_F32 : BF_BF16X3;
+}
+void* bbuf(mem_ctx* c) {
+    return c->prec == MEM_PREC_FP64_DIRECT ? (void*)c->bf64
+           : c->prec == MEM_PREC_FP32_DIRECT ? (void*)c->bf32 : (void*)c->planes;
+}
+
+// prep + forward for one image source.  mode: FwdMode.
+mem_status run_forward(mem_ctx* c, const ImgSrc& src, int mode, bool entropy, void* yout) {
+    DevData d = c->dd();
+    {
+        KTimer t(c, "prep");
+        launch_prep(d, src, bformat(c->prec), bbuf(c), entropy ? c->ent_part : nullptr, c->st);
+    }
+    c->launches++;
+    TRY(after_launch(c, "prep kernel"));
+    if (c->prec == MEM_PREC_BF16X3) {
+        KTimer t(c, "fwd_tc");
+        launch_fwd_tc(d, c->tiles, c->n_tiles, c->planes, mode, (float2*)yout, c->chi_part,
+                      c->num_sms, c->spin, c->dstatus, c->st);
+    } else {
+        KTimer t(c, c->prec == MEM_PREC_FP64_DIRECT ? "fwd_direct_f64" : "fwd_direct_f32");
+        launch_fwd_direct(d, c->prec == MEM_PREC_FP64_DIRECT, c->tiles, c->n_tiles, bbuf(c), mode, yout,
+                          c->chi_part, c->st);
+    }
+    if (c->n_tiles > 0) c->launches++;
+    TRY(after_launch(c, "forward kernel"));
+    if (mode != FWD_VIS) {
+        KTimer t(c, "scalars");
+        launch_scalars(d, c->tile_off, c->chi_part, c->ent_part, entropy ? 1 : 0, c->scal, c->img_tmp, c->st);
+        c->launches += 2;
+        TRY(after_launch(c, "scalar reduction"));
+    }
+    return MEM_OK;
+}
+
+// adjoint of y (already in y32 / y64) into gsum; returns ks used.
+mem_status run_adjoint(mem_ctx* c, int* ks_out) {
+    DevData d = c->dd();
+    if (c->prec == MEM_PREC_BF16X3) {
+        if (c->adj_ctas > 0) {
+            KTimer t(c, "adj_tc");
+            launch_adj_tc(d, c->units, c->cta_off, c->adj_ctas, c->y32, c->partial, c->spin, c->dstatus, c->st);
+            c->launches++;
+            TRY(after_launch(c, "adjoint kernel"));
+        }
+        KTimer t(c, "adj_tc_reduce");
+        launch_adj_tc_reduce(d, c->units, c->cb_off, c->partial, c->gsum, c->st);
+        c->launches++;
+        TRY(after_launch(c, "adjoint reduction"));
+        *ks_out = 1;
+    } else {
+        int ks = adj_direct_splits(d, c->num_sms);
+        const void* y = c->prec == MEM_PREC_FP64_DIRECT ? (const void*)c->y64 : (const void*)c->y32;
+        KTimer t(c, c->prec == MEM_PREC_FP64_DIRECT ? "adj_direct_f64" : "adj_direct_f32");
+        launch_adj_direct(d, c->prec == MEM_PREC_FP64_DIRECT, y, c->gsum, ks, c->st);
+        c->launches++;
+        TRY(after_launch(c, "adjoint kernel"));
+        *ks_out = ks;
+    }
+    return MEM_OK;
+}
+
+// Objective + gradient at `src`; gradient outputs optional.
+mem_status run_objgrad(mem_ctx* c, const ImgSrc& src, int projected, float* out32, double* full64,
+                       double* proj64) {
+    TRY(ensure_buffers(c));
+    void* yout = c->prec == MEM_PREC_FP64_DIRECT ? (void*)c->y64 : (void*)c->y32;
+    TRY(run_forward(c, src, FWD_RESID, true, yout));
+    int ks = 1;
+    TRY(run_adjoint(c, &ks));
+    {
+        KTimer t(c, "finalize");
+        launch_finalize(c->dd(), src, c->gsum, ks, projected, out32, full64, proj64, c->st);
+    }
+    c->launches++;
+    return after_launch(c, "gradient assembly");
+}
+
+mem_status read_scalars(mem_ctx* c, std::vector<double>& out) {
+    out.resize(3 + 3 * (size_t)c->n_images);
+    CK(cudaMemcpyAsync(out.data(), c->scal, out.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st),
+       "scalar readback");
+    TRY(check_status(c));
+    for (double x : out)
+        if (!std::isfinite(x)) return fail(c, MEM_ENUMERIC, "objective is not finite (pixels <= 0?)");
+    return MEM_OK;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* mem_status_string(mem_status s) {
+    switch (s) {
+        case MEM_OK: return "ok";
+        case MEM_EINVAL: return "invalid argument";
+        case MEM_ENOMEM: return "out of device memory";
+        case MEM_ECUDA: return "CUDA error";
+        case MEM_ETIMEOUT: return "device wait timed out";
+        case MEM_ENUMERIC: return "non-finite objective";
+        case MEM_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+const char* mem_last_error(const mem_ctx* c) { return c ? c->err.c_str() : g_last_error.c_str(); }
+
+int64_t mem_num_vis(const mem_ctx* c) { return c ? c->Z : 0; }
+int32_t mem_num_images(const mem_ctx* c) { return c ? c->n_images : 0; }
+int64_t mem_launch_count(const mem_ctx* c) { return c ? c->launches : 0; }
+const double* mem_scalars_dev(const mem_ctx* c) { return c ? c->scal : nullptr; }
+
+mem_status mem_profile(mem_ctx* c, int32_t enable) {
+    if (!c) return fail(nullptr, MEM_EINVAL, "null context");
+    c->profiling = enable != 0;
+    return MEM_OK;
+}
+
+int32_t mem_profile_read(mem_ctx* c, int32_t max_kernels, char* names, double* ms_total,
+                         int64_t* launches) {
+    if (!c) return -1;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return -1;
+    for (auto& k : c->kev) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, k.a, k.b);
+        auto& acc = c->kacc[k.name];
+        acc.first += ms;
+        acc.second += 1;
+        c->ev_pool.push_back(k.a);
+        c->ev_pool.push_back(k.b);
+    }
+    c->kev.clear();
+    int32_t i = 0;
+    for (auto& kv : c->kacc) {
+        if (i >= max_kernels) break;
+        if (names) {
+            std::strncpy(names + 32 * i, kv.first.c_str(), 31);
+            names[32 * i + 31] = 0;
+        }
+        if (ms_total) ms_total[i] = kv.second.first;
+        if (launches) launches[i] = kv.second.second;
+        ++i;
+    }
+    c->kacc.clear();
+    return i;
+}
+
+void mem_destroy(mem_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    for (auto& k : c->kev) {
+        cudaEventDestroy(k.a);
+        cudaEventDestroy(k.b);
+    }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+mem_status mem_set_precision(mem_ctx* c, int32_t prec) {
+    if (!c) return fail(nullptr, MEM_EINVAL, "null context");
+    if (prec < MEM_PREC_FP64_DIRECT || prec > MEM_PREC_BF16X3)
+        return fail(c, MEM_EINVAL, "unknown precision %d", prec);
+    if (prec == MEM_PREC_BF16X3 && !tc_shape_ok(c->N))
+        return fail(c, MEM_ENOTSUP, "BF16X3 form needs N = 64, 128 or a multiple of 256 (N = %d)", c->N);
+    c->prec = prec;
+    return ensure_buffers(c);
+}
+
+mem_status mem_create(const mem_config* cfg, const double* u, const double* v, const double* vis_obs,
+                      const double* sigma, const float* pb, void* stream, mem_ctx** out) {
+    if (!out) return fail(nullptr, MEM_EINVAL, "out is null");
+    *out = nullptr;
+    if (!cfg || !cfg->vis_offsets || !pb) return fail(nullptr, MEM_EINVAL, "null cfg, vis_offsets or pb");
+    const int N = cfg->n, C = cfg->n_channels;
+    if (N < 16 || N > 4096 || N % 16 != 0) return fail(nullptr, MEM_EINVAL, "n = %d must be a multiple of 16 in [16, 4096]", N);
+    if (C < 1) return fail(nullptr, MEM_EINVAL, "n_channels = %d", C);
+    if (!(cfg->dx > 0) || !(cfg->dy > 0)) return fail(nullptr, MEM_EINVAL, "pixel size must be > 0");
+    if (!(cfg->G > 0) || !(cfg->lambda >= 0) || !std::isfinite(cfg->G) || !std::isfinite(cfg->lambda))
+        return fail(nullptr, MEM_EINVAL, "need G > 0 and lambda >= 0");
+    if (cfg->precision < MEM_PREC_FP64_DIRECT || cfg->precision > MEM_PREC_BF16X3)
+        return fail(nullptr, MEM_EINVAL, "unknown precision %d", cfg->precision);
+    if (cfg->image_mode != MEM_IMAGES_PER_CHANNEL && cfg->image_mode != MEM_IMAGE_SHARED)
+        return fail(nullptr, MEM_EINVAL, "unknown image mode %d", cfg->image_mode);
+    if (cfg->precision == MEM_PREC_BF16X3 && !tc_shape_ok(N))
+        return fail(nullptr, MEM_ENOTSUP, "BF16X3 form needs N = 64, 128 or a multiple of 256 (N = %d)", N);
+    if (cfg->vis_offsets[0] != 0) return fail(nullptr, MEM_EINVAL, "vis_offsets[0] must be 0");
+    for (int i = 0; i < C; ++i)
+        if (cfg->vis_offsets[i + 1] < cfg->vis_offsets[i]) return fail(nullptr, MEM_EINVAL, "vis_offsets must not decrease");
+    const int64_t Z = cfg->vis_offsets[C];
+    if (Z > 0 && (!u || !v || !vis_obs || !sigma)) return fail(nullptr, MEM_EINVAL, "null visibility arrays");
+    if (Z >= ((int64_t)1 << 40)) return fail(nullptr, MEM_EINVAL, "too many visibilities");
+    for (int64_t k = 0; k < Z; ++k)
+        if (!(sigma[k] > 0) || !std::isfinite(sigma[k]) || !std::isfinite(u[k]) || !std::isfinite(v[k]))
+            return fail(nullptr, MEM_EINVAL, "sigma must be > 0 and u, v finite (index %lld)", (long long)k);
+
+    mem_ctx* c = new mem_ctx();
+    c->N = N;
+    c->C = C;
+    c->shared = cfg->image_mode == MEM_IMAGE_SHARED;
+    c->n_images = c->shared ? 1 : C;
+    c->prec = cfg->precision;
+    c->dx = cfg->dx;
+    c->dy = cfg->dy;
+    c->lambda = cfg->lambda;
+    c->G = cfg->G;
+    c->spin = cfg->spin_limit ? cfg->spin_limit : ((uint64_t)1 << 26);
+    c->Z = Z;
+    c->off.assign(cfg->vis_offsets, cfg->vis_offsets + C + 1);
+    c->st = (cudaStream_t)stream;
+    c->cap = alloc_cap();
+
+    auto bail = [&](mem_status s) {
+        mem_destroy(c);
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    cudaDeviceProp prop;
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, c->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(nullptr, MEM_ECUDA, "no CUDA device: %s", cudaGetErrorString(e)));
+    }
+    if (prop.major != 10 || prop.minor != 3)
+        return bail(fail(nullptr, MEM_ECUDA, "libmemsynth is built for sm_103a (GB300); device is sm_%d%d",
+                         prop.major, prop.minor));
+    c->num_sms = prop.multiProcessorCount;
+
+    const size_t NN = (size_t)N * N;
+    mem_status s;
+    if ((s = dalloc(c, &c->u, std::max<int64_t>(Z, 1))) || (s = dalloc(c, &c->v, std::max<int64_t>(Z, 1))) ||
+        (s = dalloc(c, &c->w, std::max<int64_t>(Z, 1))) || (s = dalloc(c, &c->pa, std::max<int64_t>(Z, 1))) ||
+        (s = dalloc(c, &c->pb, std::max<int64_t>(Z, 1))) || (s = dalloc(c, &c->vo, std::max<int64_t>(Z, 1))) ||
+        (s = dalloc(c, &c->beam, (size_t)C * NN)) || (s = dalloc(c, &c->doff, (size_t)C + 1)) ||
+        (s = dalloc(c, &c->dstatus, 1))) {
+        g_last_error = c->err;
+        return bail(s);
+    }
+    std::vector<double> wh((size_t)Z);
+    for (int64_t k = 0; k < Z; ++k) wh[k] = 1.0 / (sigma[k] * sigma[k]);
+    auto cpy = [&](void* dst, const void* src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->st) : cudaSuccess;
+    };
+    e = cpy(c->u, u, Z * sizeof(double));
+    if (e == cudaSuccess) e = cpy(c->v, v, Z * sizeof(double));
+    if (e == cudaSuccess) e = cpy(c->w, wh.data(), Z * sizeof(double));
+    if (e == cudaSuccess) e = cpy(c->vo, vis_obs, Z * 2 * sizeof(double));
+    if (e == cudaSuccess) e = cpy(c->beam, pb, C * NN * sizeof(float));
+    if (e == cudaSuccess) e = cpy(c->doff, c->off.data(), (C + 1) * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st);
+    if (e != cudaSuccess) {
+        cuda_fail(c, e, "upload");
+        g_last_error = c->err;
+        return bail(MEM_ECUDA);
+    }
+    launch_phase_prep(Z, c->u, c->v, c->dx, c->dy, c->pa, c->pb, c->st);
+    c->launches++;
+
+    build_tiles(c);
+    build_units(c);
+    if ((s = dalloc(c, &c->tiles, std::max<size_t>(c->tiles_h.size(), 1))) ||
+        (s = dalloc(c, &c->tile_off, c->tile_off_h.size())) ||
+        (s = dalloc(c, &c->units, std::max<size_t>(c->units_h.size(), 1))) ||
+        (s = dalloc(c, &c->cta_off, c->cta_off_h.size())) || (s = dalloc(c, &c->cb_off, c->cb_off_h.size()))) {
+        g_last_error = c->err;
+        return bail(s);
+    }
+    e = cpy(c->tiles, c->tiles_h.data(), c->tiles_h.size() * sizeof(VisTile));
+    if (e == cudaSuccess) e = cpy(c->tile_off, c->tile_off_h.data(), c->tile_off_h.size() * sizeof(int));
+    if (e == cudaSuccess) e = cpy(c->units, c->units_h.data(), c->units_h.size() * sizeof(AdjUnit));
+    if (e == cudaSuccess) e = cpy(c->cta_off, c->cta_off_h.data(), c->cta_off_h.size() * sizeof(int));
+    if (e == cudaSuccess) e = cpy(c->cb_off, c->cb_off_h.data(), c->cb_off_h.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        cuda_fail(c, e, "context setup");
+        g_last_error = c->err;
+        return bail(MEM_ECUDA);
+    }
+    if ((s = ensure_buffers(c)) != MEM_OK) {
+        g_last_error = c->err;
+        return bail(s);
+    }
+    *out = c;
+    return MEM_OK;
+}
+
+mem_status mem_sync(mem_ctx* c) {
+    if (!c) return fail(nullptr, MEM_EINVAL, "null context");
+    CK(cudaGetLastError(), "pending launch error");
+    return check_status(c);
+}
+
+mem_status mem_forward(mem_ctx* c, const float* image_dev, float* vis_dev) {
+    if (!c || !image_dev || (!vis_dev && c->Z > 0)) return fail(c, MEM_EINVAL, "null argument");
+    if (!aligned(vis_dev, 8)) return fail(c, MEM_EINVAL, "vis_dev must be 8-byte aligned");
+    TRY(ensure_buffers(c));
+    ImgSrc src{image_dev, nullptr, nullptr, nullptr, c->G};
+    if (c->prec == MEM_PREC_FP64_DIRECT) {
+        TRY(run_forward(c, src, FWD_VIS, false, c->y64));
+        launch_f64_to_f32(2 * c->Z, (const double*)c->y64, vis_dev, c->st);
+        c->launches++;
+        return after_launch(c, "conversion");
+    }
+    return run_forward(c, src, FWD_VIS, false, vis_dev);
+}
+
+namespace {
+__global__ void k_f32_to_f64(int64_t n, const float* __restrict__ in, double* __restrict__ out) {
+    int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (p < n) out[p] = (double)in[p];
+}
+}  // namespace
+
+mem_status mem_adjoint(mem_ctx* c, const float* y_dev, float* img_dev) {
+    if (!c || !img_dev || (!y_dev && c->Z > 0)) return fail(c, MEM_EINVAL, "null argument");
+    if (!aligned(y_dev, 8)) return fail(c, MEM_EINVAL, "y_dev must be 8-byte aligned");
+    TRY(ensure_buffers(c));
+    if (c->Z > 0) {
+        if (c->prec == MEM_PREC_FP64_DIRECT) {
+            k_f32_to_f64<<<(unsigned)((2 * c->Z + 255) / 256), 256, 0, c->st>>>(2 * c->Z, y_dev, (double*)c->y64);
+        } else {
+            CK(cudaMemcpyAsync(c->y32, y_dev, (size_t)c->Z * sizeof(float2), cudaMemcpyDeviceToDevice, c->st),
+               "copy y");
+        }
+        c->launches += (c->prec == MEM_PREC_FP64_DIRECT);
+    }
+    int ks = 1;
+    TRY(run_adjoint(c, &ks));
+    // beam factor and channel sum only: lambda = 0 view of the assembly
+    DevData d = c->dd();
+    d.lambda = 0.0;
+    ImgSrc src{nullptr, nullptr, nullptr, nullptr, c->G};
+    // the assembly reads pixel values only for the entropy term and projection;
+    // give it the output buffer as a harmless source (lambda = 0, no projection)
+    src.f32 = img_dev;
+    launch_finalize(d, src, c->gsum, ks, 0, img_dev, nullptr, nullptr, c->st);
+    c->launches++;
+    return after_launch(c, "adjoint assembly");
+}
+
+mem_status mem_objective_grad(mem_ctx* c, const float* image_dev, float* grad_dev, int32_t projected,
+                              double* out3_host) {
+    if (!c || !image_dev) return fail(c, MEM_EINVAL, "null argument");
+    ImgSrc src{image_dev, nullptr, nullptr, nullptr, c->G};
+    TRY(run_objgrad(c, src, projected, grad_dev, nullptr, nullptr));
+    if (out3_host) {
+        std::vector<double> sc;
+        TRY(read_scalars(c, sc));
+        out3_host[0] = sc[0];
+        out3_host[1] = sc[1];
+        out3_host[2] = sc[2];
+    }
+    return MEM_OK;
+}
+
+mem_status mem_objective_grad_host(mem_ctx* c, const float* image_host, float* grad_host, int32_t projected,
+                                   double* out3_host) {
+    if (!c || !image_host) return fail(c, MEM_EINVAL, "null argument");
+    const size_t n = (size_t)c->n_images * c->N * c->N;
+    TRY(dalloc(c, &c->stage, 2 * n));
+    float* dimg = c->stage;
+    float* dgrad = grad_host ? c->stage + n : nullptr;
+    CK(cudaMemcpyAsync(dimg, image_host, n * sizeof(float), cudaMemcpyHostToDevice, c->st), "image upload");
+    TRY(mem_objective_grad(c, dimg, dgrad, projected, nullptr));
+    if (grad_host)
+        CK(cudaMemcpyAsync(grad_host, dgrad, n * sizeof(float), cudaMemcpyDeviceToHost, c->st), "gradient download");
+    std::vector<double> sc;
+    TRY(read_scalars(c, sc));
+    if (out3_host) {
+        out3_host[0] = sc[0];
+        out3_host[1] = sc[1];
+        out3_host[2] = sc[2];
+    }
+    return MEM_OK;
+}
+
+mem_status mem_solve(mem_ctx* c, float* image_dev_inout, int32_t n_iter, mem_solve_report* rep,
+                     double* hist_host) {
+    if (!c || !image_dev_inout || n_iter < 0) return fail(c, MEM_EINVAL, "bad argument");
+    const int NI = c->n_images;
+    const size_t n = (size_t)NI * c->N * c->N;
+    TRY(ensure_buffers(c));
+    TRY(dalloc(c, &c->I64, n));
+    TRY(dalloc(c, &c->d64, n));
+    TRY(dalloc(c, &c->g64, n));
+    TRY(dalloc(c, &c->gf64, n));
+    TRY(dalloc(c, &c->gp64, n));
+    TRY(dalloc(c, &c->alpha, (size_t)NI));
+    TRY(dalloc(c, &c->beta, (size_t)NI));
+    TRY(dalloc(c, &c->mode, (size_t)NI));
+    TRY(dalloc(c, &c->dots, (size_t)2 * NI));
+    TRY(dalloc(c, &c->dpart, (size_t)2 * NI * prep_blocks(c->N)));
+    DevData d = c->dd();
+    cudaStream_t st = c->st;
+
+    std::vector<double> sc, hd(2 * NI), alpha(NI, 0.0), beta(NI, 0.0), phi(NI), chi(NI), S(NI), slope(NI);
+    std::vector<int> mode(NI, 0), active(NI, 1), iters(NI, 0), evals_tot(NI, 0);
+    std::vector<double> hist((size_t)NI * (n_iter + 1) * 6, 0.0);
+    int stopped_early = 0;
+
+    auto objgrad = [&]() -> mem_status {
+        ImgSrc src{nullptr, c->I64, nullptr, nullptr, c->G};
+        TRY(run_objgrad(c, src, 1, nullptr, c->gf64, c->g64));
+        TRY(read_scalars(c, sc));
+        for (int i = 0; i < NI; ++i) {
+            phi[i] = sc[3 + 3 * i];
+            chi[i] = sc[4 + 3 * i];
+            S[i] = sc[5 + 3 * i];
+        }
+        return MEM_OK;
+    };
+    auto put_hist = [&](int i, int k, double a, double b, double ev) {
+        double* h = &hist[((size_t)i * (n_iter + 1) + k) * 6];
+        h[0] = phi[i];
+        h[1] = chi[i];
+        h[2] = S[i];
+        h[3] = a;
+        h[4] = b;
+        h[5] = ev;
+    };
+    auto dots = [&](int which, const double* a, const double* b, const double* cc) -> mem_status {
+        launch_dots(d, which, a, b, cc, c->dpart, c->dots, st);
+        c->launches += 2;
+        TRY(after_launch(c, "dot products"));
+        CK(cudaMemcpyAsync(hd.data(), c->dots, 2 * NI * sizeof(double), cudaMemcpyDeviceToHost, st), "dots");
+        CK(cudaStreamSynchronize(st), "dots sync");
+        return MEM_OK;
+    };
+    auto set_dev = [&](void* dst, const void* src, size_t bytes) -> mem_status {
+        CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "upload");
+        return MEM_OK;
+    };
+
+    launch_clip_f32_to_f64(d, image_dev_inout, c->I64, st);
+    c->launches++;
+    TRY(objgrad());
+    for (int i = 0; i < NI; ++i) put_hist(i, 0, 0.0, 0.0, 0.0);
+
+    int k_done = 0;
+    for (int k = 0; k < n_iter; ++k) {
+        bool any = false;
+        for (int i = 0; i < NI; ++i) any |= active[i] != 0;
+        if (!any) break;
+        // Polak-Ribiere beta (clipped at 0), restart every RESTART iterations
+        for (int i = 0; i < NI; ++i) beta[i] = 0.0;
+        if (k > 0 && k % RESTART != 0) {
+            TRY(dots(DOT_BETA, c->g64, c->gp64, nullptr));
+            for (int i = 0; i < NI; ++i) {
+                double gg = hd[2 * i], pr = hd[2 * i + 1];
+                if (gg > 0.0) beta[i] = std::max(0.0, pr / gg);
+            }
+        }
+        for (int i = 0; i < NI; ++i) mode[i] = active[i] ? (beta[i] == 0.0 ? 2 : 1) : 0;
+        TRY(set_dev(c->beta, beta.data(), NI * sizeof(double)));
+        TRY(set_dev(c->mode, mode.data(), NI * sizeof(int)));
+        launch_cg_direction(d, c->I64, c->g64, c->beta, c->mode, c->d64, st);
+        c->launches++;
+        TRY(dots(DOT_SLOPE, c->gf64, c->d64, c->g64));
+        bool need_restart = false;
+        for (int i = 0; i < NI; ++i) {
+            slope[i] = hd[2 * i];
+            mode[i] = 0;
+            if (active[i] && slope[i] >= 0.0) {
+                mode[i] = 2;
+                beta[i] = 0.0;
+                need_restart = true;
+            }
+        }
+        if (need_restart) {
+            TRY(set_dev(c->mode, mode.data(), NI * sizeof(int)));
+            launch_cg_direction(d, c->I64, c->g64, c->beta, c->mode, c->d64, st);
+            c->launches++;
+            TRY(dots(DOT_SLOPE, c->gf64, c->d64, c->g64));
+            for (int i = 0; i < NI; ++i)
+                if (mode[i] == 2) slope[i] = hd[2 * i];
+        }
+        for (int i = 0; i < NI; ++i)
+            if (active[i] && slope[i] >= 0.0) {
+                active[i] = 0;
+                stopped_early = 1;
+            }
+        // quadratic model of chi^2 along d: curvature sum w |F(A d)|^2
+        {
+            ImgSrc src{nullptr, c->d64, nullptr, nullptr, c->G};
+            TRY(run_forward(c, src, FWD_CURV, false, nullptr));
+            TRY(read_scalars(c, sc));
+        }
+        std::vector<LineSearch> ls(NI);
+        std::vector<double> alpha0(NI, 0.0);
+        bool need_max = false;
+        for (int i = 0; i < NI; ++i) {
+            if (!active[i]) continue;
+            double curv = 2.0 * sc[4 + 3 * i];
+            if (curv > 0.0) alpha0[i] = -slope[i] / curv;
+            else need_max = true;
+        }
+        if (need_max) {
+            TRY(dots(DOT_MAX, c->I64, c->d64, nullptr));
+            for (int i = 0; i < NI; ++i)
+                if (active[i] && !(alpha0[i] > 0.0)) alpha0[i] = hd[2 * i] / hd[2 * i + 1];
+        }
+        for (int i = 0; i < NI; ++i)
+            if (active[i]) ls[i].start(phi[i], alpha0[i]);
+        // batched line searches: one objective evaluation serves every image
+        for (;;) {
+            bool running = false;
+            for (int i = 0; i < NI; ++i) {
+                alpha[i] = (active[i] && ls[i].running()) ? ls[i].req : 0.0;
+                running |= active[i] && ls[i].running();
+            }
+            if (!running) break;
+            TRY(set_dev(c->alpha, alpha.data(), NI * sizeof(double)));
+            ImgSrc src{nullptr, c->I64, c->d64, c->alpha, c->G};
+            TRY(run_forward(c, src, FWD_CHI, true, nullptr));
+            TRY(read_scalars(c, sc));
+            for (int i = 0; i < NI; ++i)
+                if (active[i] && ls[i].running()) ls[i].feed(sc[3 + 3 * i]);
+        }
+        for (int i = 0; i < NI; ++i) {
+            alpha[i] = 0.0;
+            if (!active[i]) continue;
+            if (ls[i].alpha <= 0.0) {
+                active[i] = 0;
+                stopped_early = 1;
+                continue;
+            }
+            alpha[i] = ls[i].alpha;
+        }
+        TRY(set_dev(c->alpha, alpha.data(), NI * sizeof(double)));
+        launch_cg_step(d, c->I64, c->d64, c->alpha, st);
+        CK(cudaMemcpyAsync(c->gp64, c->g64, n * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy g");
+        c->launches++;
+        std::vector<double> phi_old = phi, chi_old = chi, S_old = S;
+        TRY(objgrad());
+        for (int i = 0; i < NI; ++i) {
+            if (alpha[i] > 0.0) {
+                iters[i] = k + 1;
+                evals_tot[i] += ls[i].evals + 2;
+                put_hist(i, k + 1, alpha[i], beta[i], (double)(ls[i].evals + 2));
+            } else {
+                phi[i] = phi_old[i];
+                chi[i] = chi_old[i];
+                S[i] = S_old[i];
+                put_hist(i, k + 1, 0.0, 0.0, 0.0);
+            }
+        }
+        k_done = k + 1;
+    }
+    for (int k = k_done + 1; k <= n_iter; ++k)
+        for (int i = 0; i < NI; ++i) put_hist(i, k, 0.0, 0.0, 0.0);
+    launch_f64_to_f32((int64_t)n, c->I64, image_dev_inout, st);
+    c->launches++;
+    TRY(after_launch(c, "image download"));
+    TRY(check_status(c));
+    if (hist_host) std::memcpy(hist_host, hist.data(), hist.size() * sizeof(double));
+    if (rep) {
+        rep->iterations = *std::max_element(iters.begin(), iters.end());
+        rep->evaluations = 0;
+        for (int x : evals_tot) rep->evaluations += x;
+        rep->status = MEM_OK;
+        rep->stopped_early = stopped_early;
+        rep->phi = rep->chi2 = rep->entropy = 0.0;
+        for (int i = 0; i < NI; ++i) {
+            rep->phi += phi[i];
+            rep->chi2 += chi[i];
+            rep->entropy += S[i];
+        }
+    }
+    return MEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Internal interfaces of libmemsynth: device data views and kernel launchers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace msk {
+
+// Device status word bits (the host maps them to mem_status).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADARG = 2 };
+
+// 128 consecutive visibilities of one channel (the forward kernels' unit).
+struct VisTile {
+    int32_t chan;
+    int32_t count;
+    int64_t start;
+};
+
+// Split-K unit of the tensor-core adjoint: one output block of one channel
+// over a visibility range.
+struct AdjUnit {
+    int32_t chan;
+    int32_t block;   // output block index (row-major over N/BLK x N/BLK)
+    int64_t start;   // first visibility (global index)
+    int64_t count;
+};
+
+// Read-only problem data resident on the device.
+struct DevData {
+    int N;
+    int C;
+    int n_images;
+    int shared;          // 1: one image for all channels
+    double G;
+    double lambda;
+    const uint64_t* pa;  // frac(u dx) as 64-bit fixed-point turns
+    const uint64_t* pb;  // frac(v dy)
+    const double* u;
+    const double* v;
+    const double2* vo;   // observed visibilities
+    const double* w;     // 1/sigma^2
+    const float* beam;   // C*N*N
+    const int64_t* off;  // C+1
+};
+
+// Where pixel values come from: the caller's FP32 image, or the solver's FP64
+// state, optionally moved along a direction and clipped: max(I + alpha_i d, G).
+struct ImgSrc {
+    const float* f32;
+    const double* f64;
+    const double* dir;
+    const double* alpha;  // per image (device)
+    double G;
+};
+
+enum BFormat { BF_F32 = 0, BF_F64 = 1, BF_BF16X3 = 2 };
+enum FwdMode { FWD_VIS = 0, FWD_RESID = 1, FWD_CHI = 2, FWD_CURV = 3 };
+
+// Forward tensor-core tiling: m-block width and n per pipeline stage.
+constexpr int TC_BK = 32;
+inline int tc_bn(int N) { return N < 128 ? N : 128; }
+// Adjoint tensor-core tiling: output block side and visibilities per stage.
+constexpr int TCA_BK = 16;
+inline int tca_blk(int N) { return N < 256 ? N : 256; }
+
+// ---- launchers (all asynchronous on `st`) ----
+void launch_phase_prep(int64_t Z, const double* u, const double* v, double dx, double dy,
+                       uint64_t* pa, uint64_t* pb, cudaStream_t st);
+
+// B_c = A_c * img(c) for every channel in the requested format; entropy
+// partials S_i per (image, block) when ent_part != nullptr.
+void launch_prep(const DevData& d, const ImgSrc& src, int fmt, void* bout, double* ent_part,
+                 cudaStream_t st);
+int prep_blocks(int N);
+
+void launch_fwd_direct(const DevData& d, int fp64, const VisTile* tiles, int n_tiles, const void* B,
+                       int mode, void* yout, double* chi_part, cudaStream_t st);
+// gsum: [ks][C][N*N] doubles, per-channel sums without the beam factor.
+void launch_adj_direct(const DevData& d, int fp64, const void* y, double* gsum, int ks,
+                       cudaStream_t st);
+int adj_direct_splits(const DevData& d, int num_sms);
+
+// Tensor-core forms.
+int fwd_tc_smem_bytes(int N);
+void launch_fwd_tc(const DevData& d, const VisTile* tiles, int n_tiles, const void* planes,
+                   int mode, float2* yout, double* chi_part, int grid, uint64_t spin, int* status,
+                   cudaStream_t st);
+int adj_tc_smem_bytes(int N);
+// units sorted by CTA: CTA b runs units [cta_unit_off[b], cta_unit_off[b+1]).
+void launch_adj_tc(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
+                   const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st);
+// Sum unit partials per channel (unit order) into gsum[C][N*N].
+void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* unit_off_by_chan_blk,
+                          const float* partial, double* gsum, cudaStream_t st);
+
+// grad_i = sum_{c in image i} A_c * sum_k gsum[k][c] + lambda (1 + log(I/G)); optional projection.
+void launch_finalize(const DevData& d, const ImgSrc& src, const double* gsum, int ks, int projected,
+                     float* out32, double* full64, double* proj64, cudaStream_t st);
+
+// chi_part holds 4 partials per visibility tile (one per 32 visibilities).
+// Per-image chi^2 / S / Phi into scal[3 + 3 i ...] and totals into scal[0..2].
+void launch_scalars(const DevData& d, const int* tile_off, const double* chi_part,
+                    const double* ent_part, int with_entropy, double* scal, double* img_tmp,
+                    cudaStream_t st);
+
+// Solver vector kernels (FP64, per image).
+void launch_dots(const DevData& d, int which, const double* a, const double* b, const double* c,
+                 double* part, double* out, cudaStream_t st);
+void launch_cg_direction(const DevData& d, const double* I, const double* g, const double* beta,
+                         const int* mode, double* dir, cudaStream_t st);
+void launch_cg_step(const DevData& d, double* I, const double* dir, const double* alpha,
+                    cudaStream_t st);
+void launch_clip_f32_to_f64(const DevData& d, const float* in, double* out, cudaStream_t st);
+void launch_f64_to_f32(int64_t n, const double* in, float* out, cudaStream_t st);
+
+enum DotKind { DOT_BETA = 0, DOT_SLOPE = 1, DOT_MAX = 2 };
+
+}  // namespace msk

@@ -1,0 +1,620 @@
+// Tensor-core (tcgen05) forms of the measurement operator and its adjoint.
+//
+// On the regular pixel grid the phase of Eq. (1) separates,
+//   exp(-2 pi i (u x_m + v y_n)) = Ex[k,m] Ey[k,n],
+//   Ex[k,m] = exp(-2 pi i u_k x_m),  Ey[k,n] = exp(-2 pi i v_k y_n),
+// so the forward sum is   V_k = sum_m Ex[k,m] T[k,m],  T = Ey B^T  (B = A*I),
+// and the chi^2 gradient (Eq. chi2gradient, Appendix C) is
+//   G[n,m] = sum_k Re(Ey)[k,n] Re(P)[k,m] + Im(Ey)[k,n] Im(P)[k,m],
+//   P[k,m] = y_k conj(Ex[k,m]),  y = w r.
+// Both contractions run on the 5th-generation tensor cores (tcgen05.mma,
+// kind::f16, accumulators in TMEM) in 3-term split BF16: x = hi + lo,
+// a b ~= a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32 accumulation.  The phase
+// tables are never stored: producer warps generate each tile in shared
+// memory from the exact fixed-point phases (one SFU sincos per 8 entries,
+// the rest by complex rotation), already split and laid out as UMMA operands.
+//
+// Every mbarrier wait is bounded; a wait that runs out sets the device status
+// word and the whole CTA unwinds, releasing its TMEM.
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace msk {
+
+// exp(-i 2 pi p) as (cos, -sin), p a fixed-point phase; SFU sincos of an angle
+// reduced exactly to [-pi, pi).
+__device__ __forceinline__ cf2 cis_neg(uint64_t p) {
+    float s, c;
+    __sincosf(phase_to_angle_f32(p), &s, &c);
+    return {c, -s};
+}
+
+// ===========================================================================
+// Forward: T = Ey B^T on tensor cores, fused V_k = sum_m Ex T, residual, chi^2.
+// CTA roles: warps 0-3 epilogue (TMEM lanes 0-127 = the tile's 128
+// visibilities), warp 4 MMA issuer + TMEM owner, warp 5 bulk copies of the
+// image operand, warps 6-13 phase-table producers.
+// ===========================================================================
+constexpr int FWD_STAGES = 4;
+constexpr int FWD_THREADS = 448;
+constexpr int FWD_A_PLANE = 128 * TC_BK * 2;       // bytes per A plane (8 KB)
+constexpr int FWD_A_BYTES = 4 * FWD_A_PLANE;        // Re hi, Re lo, Im hi, Im lo
+
+__host__ __device__ inline int fwd_stage_bytes(int BN) { return FWD_A_BYTES + 2 * BN * TC_BK * 2; }
+
+int fwd_tc_smem_bytes(int N) { return FWD_STAGES * fwd_stage_bytes(tc_bn(N)) + 1024; }
+
+struct FwdShared {
+    uint64_t full[FWD_STAGES];   // producer warps (8 arrivals)
+    uint64_t bfull[FWD_STAGES];  // image operand bulk copy (transaction count)
+    uint64_t empty[FWD_STAGES];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__global__ void __launch_bounds__(FWD_THREADS, 1)
+    k_fwd_tc(DevData d, const VisTile* __restrict__ tiles, int n_tiles,
+             const __nv_bfloat16* __restrict__ planes, int mode, float2* __restrict__ yout,
+             double* __restrict__ chi_part, uint64_t spin, int* status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ FwdShared S;
+    const int N = d.N, c0 = N / 2;
+    const int BN = N < 128 ? N : 128;
+    const int n_mb = N / BN, nk = N / TC_BK;
+    const int stage_bytes = fwd_stage_bytes(BN);
+    const int64_t NN = (int64_t)N * N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* abort = &S.abort;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < FWD_STAGES; ++s) {
+            mbar_init(&S.full[s], 8);
+            mbar_init(&S.bfull[s], 1);
+            mbar_init(&S.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&S.tfull[b], 1);
+            mbar_init(&S.tempty[b], 4);
+        }
+        mbar_init(&S.drain, 1);
+        S.abort = 0;
+        mbar_fence_init();
+    }
+    if (warp == 4) {
+        tmem_alloc(&S.tmem_base, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    if (warp == 4) {
+        // ------------------------------------------------------------ MMA
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(128, BN, 0, 0);
+            const uint32_t sbase = smem_u32(smem);
+            uint32_t sc = 0, it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                for (int mb = 0; mb < n_mb && ok; ++mb, ++it) {
+                    const int b = it & 1;
+                    ok = mbar_wait(&S.tempty[b], ((it >> 1) & 1) ^ 1, spin, abort, status);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t d_re = tmem + (uint32_t)(b * 256);
+                    const uint32_t d_im = d_re + 128;
+                    for (int ks = 0; ks < nk; ++ks, ++sc) {
+                        const int s = sc % FWD_STAGES;
+                        ok = mbar_wait(&S.full[s], (sc / FWD_STAGES) & 1, spin, abort, status) &&
+                             mbar_wait(&S.bfull[s], (sc / FWD_STAGES) & 1, spin, abort, status);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t A = sbase + s * stage_bytes;
+                        const uint32_t B = A + FWD_A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                            const uint32_t ao = kk * 2 * 2048, bo = kk * 2 * 16 * BN;
+                            uint64_t are_h = smem_desc(A + 0 * FWD_A_PLANE + ao, 2048, 128);
+                            uint64_t are_l = smem_desc(A + 1 * FWD_A_PLANE + ao, 2048, 128);
+                            uint64_t aim_h = smem_desc(A + 2 * FWD_A_PLANE + ao, 2048, 128);
+                            uint64_t aim_l = smem_desc(A + 3 * FWD_A_PLANE + ao, 2048, 128);
+                            uint64_t b_h = smem_desc(B + bo, 16 * BN, 128);
+                            uint64_t b_l = smem_desc(B + BN * TC_BK * 2 + bo, 16 * BN, 128);
+                            uint32_t acc = (ks > 0 || kk > 0) ? 1u : 0u;
+                            umma_bf16(d_re, are_h, b_h, idesc, acc);
+                            umma_bf16(d_re, are_h, b_l, idesc, 1u);
+                            umma_bf16(d_re, are_l, b_h, idesc, 1u);
+                            umma_bf16(d_im, aim_h, b_h, idesc, acc);
+                            umma_bf16(d_im, aim_h, b_l, idesc, 1u);
+                            umma_bf16(d_im, aim_l, b_h, idesc, 1u);
+                        }
+                        umma_commit(&S.empty[s]);
+                    }
+                    if (ok) umma_commit(&S.tfull[b]);
+                }
+            }
+            // all issued MMAs complete before TMEM is released (they always
+            // finish: their operands were complete when they were issued)
+            umma_commit(&S.drain);
+            int dummy = 0;
+            mbar_wait(&S.drain, 0, 1ull << 32, (volatile int*)&dummy, status);
+        }
+        __syncwarp();
+    } else if (warp == 5) {
+        // ------------------------------------------------ image operand copies
+        if (lane == 0) {
+            uint32_t sc = 0;
+            bool ok = true;
+            const uint32_t chunk_bytes = 2u * BN * TC_BK * 2;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                const int chan = tiles[t].chan;
+                const unsigned char* cbase = (const unsigned char*)(planes + (int64_t)chan * 2 * NN);
+                for (int mb = 0; mb < n_mb && ok; ++mb) {
+                    for (int ks = 0; ks < nk; ++ks, ++sc) {
+                        const int s = sc % FWD_STAGES;
+                        ok = mbar_wait(&S.empty[s], ((sc / FWD_STAGES) & 1) ^ 1, spin, abort, status);
+                        if (!ok) break;
+                        mbar_arrive_expect_tx(&S.bfull[s], chunk_bytes);
+                        bulk_g2s(smem + s * stage_bytes + FWD_A_BYTES,
+                                 cbase + (int64_t)(mb * nk + ks) * chunk_bytes, chunk_bytes, &S.bfull[s]);
+                    }
+                }
+            }
+            if (!ok) {
+                // copies already issued land on their own; wait for them before
+                // the CTA's shared memory is released
+                int dummy = 0;
+                for (uint32_t q = (sc > FWD_STAGES ? sc - FWD_STAGES : 0); q < sc; ++q)
+                    mbar_wait(&S.bfull[q % FWD_STAGES], (q / FWD_STAGES) & 1, 1ull << 32,
+                              (volatile int*)&dummy, status);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 6) {
+        // ------------------------------------------- Ey tile producers (256 thr)
+        const int ptid = threadIdx.x - 192;
+        const int row = ptid & 127;
+        uint32_t sc = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            const VisTile tl = tiles[t];
+            const bool valid = row < tl.count;
+            const uint64_t pb = valid ? d.pb[tl.start + row] : 0;
+            cf2 step[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) step[q] = cis_neg(phase_mul(q, pb));
+            for (int mb = 0; mb < n_mb && ok; ++mb) {
+                for (int ks = 0; ks < nk; ++ks, ++sc) {
+                    const int s = sc % FWD_STAGES;
+                    ok = __all_sync(0xffffffffu,
+                                    mbar_wait(&S.empty[s], ((sc / FWD_STAGES) & 1) ^ 1, spin, abort, status));
+                    if (!ok) break;
+                    unsigned char* A = smem + s * stage_bytes;
+#pragma unroll
+                    for (int gi = 0; gi < 2; ++gi) {
+                        const int g = (ptid >> 7) + 2 * gi;  // k-group (8 image rows n)
+                        uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
+                        if (valid) {
+                            const int n0 = ks * TC_BK + g * 8;
+                            const cf2 base = cis_neg(phase_mul(n0 - c0, pb));
+                            cf2 z[8];
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) z[q] = cmul(base, step[q]);
+                            split_bf16x2(z[0].x, z[1].x, rh.x, rl.x);
+                            split_bf16x2(z[2].x, z[3].x, rh.y, rl.y);
+                            split_bf16x2(z[4].x, z[5].x, rh.z, rl.z);
+                            split_bf16x2(z[6].x, z[7].x, rh.w, rl.w);
+                            split_bf16x2(z[0].y, z[1].y, ih.x, il.x);
+                            split_bf16x2(z[2].y, z[3].y, ih.y, il.y);
+                            split_bf16x2(z[4].y, z[5].y, ih.z, il.z);
+                            split_bf16x2(z[6].y, z[7].y, ih.w, il.w);
+                        }
+                        const int off = (g * 16 + (row >> 3)) * 128 + (row & 7) * 16;
+                        *(uint4*)(A + 0 * FWD_A_PLANE + off) = rh;
+                        *(uint4*)(A + 1 * FWD_A_PLANE + off) = rl;
+                        *(uint4*)(A + 2 * FWD_A_PLANE + off) = ih;
+                        *(uint4*)(A + 3 * FWD_A_PLANE + off) = il;
+                    }
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S.full[s]);
+                }
+            }
+        }
+    } else {
+        // ------------------------------------ epilogue (warps 0-3, 128 threads)
+        const int row = threadIdx.x;  // TMEM lane = visibility within tile
+        uint32_t it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            const VisTile tl = tiles[t];
+            const bool valid = row < tl.count;
+            const int64_t j = tl.start + (valid ? row : 0);
+            const uint64_t pa = d.pa[j];
+            cf2 step[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) step[q] = cis_neg(phase_mul(q, pa));
+            double vre = 0.0, vim = 0.0;
+            for (int mb = 0; mb < n_mb; ++mb, ++it) {
+                const int b = it & 1;
+                ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull[b], (it >> 1) & 1, spin, abort, status));
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 256);
+                for (int q = 0; q < BN / 16; ++q) {
+                    uint32_t tre[16], tim[16];
+                    tmem_ld16(lane_base + q * 16, tre);
+                    tmem_ld16(lane_base + 128 + q * 16, tim);
+                    tmem_ld_wait();
+                    const int m0 = mb * BN + q * 16;
+                    const cf2 base = cis_neg(phase_mul(m0 - c0, pa));
+                    float ar = 0.f, ai = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const cf2 ex = cmul(base, step[k]);
+                        const float tr = __uint_as_float(tre[k]), ti = __uint_as_float(tim[k]);
+                        ar = fmaf(ex.x, tr, fmaf(-ex.y, ti, ar));
+                        ai = fmaf(ex.x, ti, fmaf(ex.y, tr, ai));
+                    }
+                    vre += (double)ar;
+                    vim += (double)ai;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.tempty[b]);
+            }
+            if (!ok) break;
+            double chi = 0.0;
+            if (valid) {
+                if (mode == FWD_VIS) {
+                    yout[j] = make_float2((float)vre, (float)vim);
+                } else {
+                    double rr = vre, ri = vim;
+                    if (mode != FWD_CURV) { rr -= d.vo[j].x; ri -= d.vo[j].y; }
+                    const double w = d.w[j];
+                    chi = 0.5 * w * (rr * rr + ri * ri);
+                    if (mode == FWD_RESID) yout[j] = make_float2((float)(w * rr), (float)(w * ri));
+                }
+            }
+            if (mode != FWD_VIS) {
+                // one partial per warp (32 visibilities), summed later in a fixed order
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) chi += __shfl_down_sync(0xffffffffu, chi, o);
+                if (lane == 0) chi_part[(int64_t)t * 4 + warp] = chi;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+void launch_fwd_tc(const DevData& d, const VisTile* tiles, int n_tiles, const void* planes, int mode,
+                   float2* yout, double* chi_part, int grid, uint64_t spin, int* status,
+                   cudaStream_t st) {
+    if (n_tiles <= 0) return;
+    int smem = fwd_tc_smem_bytes(d.N);
+    static int configured = 0;
+    if (configured < smem) {
+        cudaFuncSetAttribute(k_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        configured = smem;
+    }
+    if (grid > n_tiles) grid = n_tiles;
+    k_fwd_tc<<<grid, FWD_THREADS, smem, st>>>(d, tiles, n_tiles, (const __nv_bfloat16*)planes, mode,
+                                              yout, chi_part, spin, status);
+}
+
+// ===========================================================================
+// Adjoint: split-K over visibilities.  A CTA owns a contiguous run of
+// (channel, output block, visibility range) units, accumulates each unit's
+// BLK x BLK block of G in TMEM over 16-visibility stages and drains it to an
+// FP32 partial buffer; partials are summed in unit order in FP64 afterwards.
+// Operands are MN-major (8 consecutive pixels of one visibility per 16-byte
+// core-matrix row), the layout the per-visibility phase recurrences produce.
+// Roles: warps 0-3 drain, warp 4 MMA + TMEM owner, warps 6-13 producers.
+// ===========================================================================
+constexpr int ADJ_STAGES = 3;
+constexpr int ADJ_THREADS = 448;
+
+__host__ __device__ inline int adj_rows(int BLK) { return BLK < 128 ? 128 : BLK; }
+__host__ __device__ inline int adj_stage_bytes(int BLK) {
+    return 4 * adj_rows(BLK) * TCA_BK * 2 + 4 * BLK * TCA_BK * 2;
+}
+int adj_tc_smem_bytes(int N) { return ADJ_STAGES * adj_stage_bytes(tca_blk(N)) + 1024; }
+__host__ __device__ inline uint32_t adj_tmem_cols(int BLK) {
+    int c = (adj_rows(BLK) / 128) * BLK;
+    uint32_t p = 32;
+    while ((int)p < c) p <<= 1;
+    return p;
+}
+
+struct AdjShared {
+    uint64_t full[ADJ_STAGES];
+    uint64_t empty[ADJ_STAGES];
+    uint64_t tfull;
+    uint64_t tempty;
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__global__ void __launch_bounds__(ADJ_THREADS, 1)
+    k_adj_tc(DevData d, const AdjUnit* __restrict__ units, const int* __restrict__ cta_unit_off,
+             const float2* __restrict__ y, float* __restrict__ partial, uint64_t spin, int* status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ AdjShared S;
+    const int N = d.N, c0 = N / 2;
+    const int BLK = N < 256 ? N : 256;
+    const int R = adj_rows(BLK);           // A rows (image rows n, padded to 128)
+    const int n_mt = R / 128;
+    const int nbx = N / BLK;
+    const int a_plane = R * TCA_BK * 2, b_plane = BLK * TCA_BK * 2;
+    const int stage_bytes = 4 * a_plane + 4 * b_plane;
+    const uint32_t tcols = adj_tmem_cols(BLK);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int u0 = cta_unit_off[blockIdx.x], u1 = cta_unit_off[blockIdx.x + 1];
+    volatile int* abort = &S.abort;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ADJ_STAGES; ++s) {
+            mbar_init(&S.full[s], 8);
+            mbar_init(&S.empty[s], 1);
+        }
+        mbar_init(&S.tfull, 1);
+        mbar_init(&S.tempty, 4);
+        mbar_init(&S.drain, 1);
+        S.abort = 0;
+        mbar_fence_init();
+    }
+    if (warp == 4) {
+        tmem_alloc(&S.tmem_base, tcols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(128, BLK, 1, 1);
+            const uint32_t sbase = smem_u32(smem);
+            uint32_t sc = 0;
+            bool ok = true;
+            for (int u = u0; u < u1 && ok; ++u) {
+                const int it = u - u0;
+                ok = mbar_wait(&S.tempty, (it & 1) ^ 1, spin, abort, status);
+                if (!ok) break;
+                tc_fence_after();
+                const int nst = (int)((units[u].count + TCA_BK - 1) / TCA_BK);
+                for (int ks = 0; ks < nst; ++ks, ++sc) {
+                    const int s = sc % ADJ_STAGES;
+                    ok = mbar_wait(&S.full[s], (sc / ADJ_STAGES) & 1, spin, abort, status);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t A = sbase + s * stage_bytes;
+                    const uint32_t B = A + 4 * a_plane;
+                    const uint32_t lboA = (uint32_t)(R / 8) * 128, lboB = (uint32_t)(BLK / 8) * 128;
+                    const uint64_t bre_h = smem_desc(B + 0 * b_plane, lboB, 128);
+                    const uint64_t bre_l = smem_desc(B + 1 * b_plane, lboB, 128);
+                    const uint64_t bim_h = smem_desc(B + 2 * b_plane, lboB, 128);
+                    const uint64_t bim_l = smem_desc(B + 3 * b_plane, lboB, 128);
+                    for (int mt = 0; mt < n_mt; ++mt) {
+                        const uint32_t ao = mt * 2048;  // 16 groups of 8 rows
+                        const uint64_t are_h = smem_desc(A + 0 * a_plane + ao, lboA, 128);
+                        const uint64_t are_l = smem_desc(A + 1 * a_plane + ao, lboA, 128);
+                        const uint64_t aim_h = smem_desc(A + 2 * a_plane + ao, lboA, 128);
+                        const uint64_t aim_l = smem_desc(A + 3 * a_plane + ao, lboA, 128);
+                        const uint32_t dt = tmem + (uint32_t)(mt * BLK);
+                        const uint32_t acc = ks > 0 ? 1u : 0u;
+                        umma_bf16(dt, are_h, bre_h, idesc, acc);
+                        umma_bf16(dt, are_h, bre_l, idesc, 1u);
+                        umma_bf16(dt, are_l, bre_h, idesc, 1u);
+                        umma_bf16(dt, aim_h, bim_h, idesc, 1u);
+                        umma_bf16(dt, aim_h, bim_l, idesc, 1u);
+                        umma_bf16(dt, aim_l, bim_h, idesc, 1u);
+                    }
+                    umma_commit(&S.empty[s]);
+                }
+                if (ok) umma_commit(&S.tfull);
+            }
+            umma_commit(&S.drain);
+            int dummy = 0;
+            mbar_wait(&S.drain, 0, 1ull << 32, (volatile int*)&dummy, status);
+        }
+        __syncwarp();
+    } else if (warp >= 6) {
+        // ------------------------------------------------ producers (256 thr)
+        const int ptid = threadIdx.x - 192;
+        const int jj = ptid & 15;           // visibility within the stage
+        const int ngA = R / 8, ngB = BLK / 8;
+        uint32_t sc = 0;
+        bool ok = true;
+        for (int u = u0; u < u1 && ok; ++u) {
+            const AdjUnit un = units[u];
+            const int blk_n0 = (un.block / nbx) * BLK, blk_m0 = (un.block % nbx) * BLK;
+            const int nst = (int)((un.count + TCA_BK - 1) / TCA_BK);
+            for (int ks = 0; ks < nst; ++ks, ++sc) {
+                const int s = sc % ADJ_STAGES;
+                ok = __all_sync(0xffffffffu,
+                                mbar_wait(&S.empty[s], ((sc / ADJ_STAGES) & 1) ^ 1, spin, abort, status));
+                if (!ok) break;
+                unsigned char* A = smem + s * stage_bytes;
+                unsigned char* B = A + 4 * a_plane;
+                const int64_t kv = (int64_t)ks * TCA_BK + jj;
+                const bool valid = kv < un.count;
+                uint64_t pa = 0, pb = 0;
+                cf2 yv = {0.f, 0.f};
+                if (valid) {
+                    pa = d.pa[un.start + kv];
+                    pb = d.pb[un.start + kv];
+                    const float2 t = y[un.start + kv];
+                    yv = {t.x, t.y};
+                }
+                // rotation steps exp(-i 2 pi q a), q = 0..7, by powers of one SFU value
+                cf2 sy[8], sx[8];
+                sy[0] = {1.f, 0.f};
+                sx[0] = {1.f, 0.f};
+                sy[1] = cis_neg(pb);
+                sx[1] = cis_neg(pa);
+                sy[2] = cmul(sy[1], sy[1]);
+                sx[2] = cmul(sx[1], sx[1]);
+                sy[4] = cmul(sy[2], sy[2]);
+                sx[4] = cmul(sx[2], sx[2]);
+                sy[3] = cmul(sy[2], sy[1]);
+                sx[3] = cmul(sx[2], sx[1]);
+                sy[5] = cmul(sy[4], sy[1]);
+                sx[5] = cmul(sx[4], sx[1]);
+                sy[6] = cmul(sy[4], sy[2]);
+                sx[6] = cmul(sx[4], sx[2]);
+                sy[7] = cmul(sy[4], sy[3]);
+                sx[7] = cmul(sx[4], sx[3]);
+                for (int item = ptid >> 4; item < ngA + ngB; item += 16) {
+                    uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
+                    unsigned char* dst;
+                    int plane;
+                    if (item < ngA) {
+                        const int g = item;
+                        const int n0 = blk_n0 + g * 8;
+                        if (valid && g * 8 < BLK) {
+                            const cf2 base = cis_neg(phase_mul(n0 - c0, pb));
+                            cf2 z[8];
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) z[q] = cmul(base, sy[q]);
+                            split_bf16x2(z[0].x, z[1].x, rh.x, rl.x);
+                            split_bf16x2(z[2].x, z[3].x, rh.y, rl.y);
+                            split_bf16x2(z[4].x, z[5].x, rh.z, rl.z);
+                            split_bf16x2(z[6].x, z[7].x, rh.w, rl.w);
+                            split_bf16x2(z[0].y, z[1].y, ih.x, il.x);
+                            split_bf16x2(z[2].y, z[3].y, ih.y, il.y);
+                            split_bf16x2(z[4].y, z[5].y, ih.z, il.z);
+                            split_bf16x2(z[6].y, z[7].y, ih.w, il.w);
+                        }
+                        dst = A + ((jj >> 3) * ngA + g) * 128 + (jj & 7) * 16;
+                        plane = a_plane;
+                    } else {
+                        const int g = item - ngA;
+                        const int m0 = blk_m0 + g * 8;
+                        if (valid) {
+                            // P = y conj(Ex): conj(base) times conj(steps)
+                            const cf2 e = cis_neg(phase_mul(m0 - c0, pa));
+                            const cf2 base = cmul(yv, cf2{e.x, -e.y});
+                            cf2 z[8];
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) z[q] = cmul(base, cf2{sx[q].x, -sx[q].y});
+                            split_bf16x2(z[0].x, z[1].x, rh.x, rl.x);
+                            split_bf16x2(z[2].x, z[3].x, rh.y, rl.y);
+                            split_bf16x2(z[4].x, z[5].x, rh.z, rl.z);
+                            split_bf16x2(z[6].x, z[7].x, rh.w, rl.w);
+                            split_bf16x2(z[0].y, z[1].y, ih.x, il.x);
+                            split_bf16x2(z[2].y, z[3].y, ih.y, il.y);
+                            split_bf16x2(z[4].y, z[5].y, ih.z, il.z);
+                            split_bf16x2(z[6].y, z[7].y, ih.w, il.w);
+                        }
+                        dst = B + ((jj >> 3) * ngB + g) * 128 + (jj & 7) * 16;
+                        plane = b_plane;
+                    }
+                    *(uint4*)(dst + 0 * plane) = rh;
+                    *(uint4*)(dst + 1 * plane) = rl;
+                    *(uint4*)(dst + 2 * plane) = ih;
+                    *(uint4*)(dst + 3 * plane) = il;
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.full[s]);
+            }
+        }
+    } else if (warp < 4) {
+        // ---------------------------------------------- drain (128 threads)
+        bool ok = true;
+        for (int u = u0; u < u1 && ok; ++u) {
+            const int it = u - u0;
+            ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull, it & 1, spin, abort, status));
+            if (!ok) break;
+            tc_fence_after();
+            float* out = partial + (int64_t)u * BLK * BLK;
+            for (int mt = 0; mt < n_mt; ++mt) {
+                const int nrow = mt * 128 + warp * 32 + lane;
+                const uint32_t lb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * BLK);
+                for (int q = 0; q < BLK / 16; ++q) {
+                    uint32_t r[16];
+                    tmem_ld16(lb + q * 16, r);
+                    tmem_ld_wait();
+                    if (nrow < BLK) {
+                        float4* o = (float4*)(out + (int64_t)nrow * BLK + q * 16);
+                        o[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]),
+                                           __uint_as_float(r[2]), __uint_as_float(r[3]));
+                        o[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]),
+                                           __uint_as_float(r[6]), __uint_as_float(r[7]));
+                        o[2] = make_float4(__uint_as_float(r[8]), __uint_as_float(r[9]),
+                                           __uint_as_float(r[10]), __uint_as_float(r[11]));
+                        o[3] = make_float4(__uint_as_float(r[12]), __uint_as_float(r[13]),
+                                           __uint_as_float(r[14]), __uint_as_float(r[15]));
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.tempty);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        tc_fence_after();
+        tmem_dealloc(tmem, tcols);
+    }
+}
+
+void launch_adj_tc(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
+                   const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st) {
+    if (n_ctas <= 0) return;
+    int smem = adj_tc_smem_bytes(d.N);
+    static int configured = 0;
+    if (configured < smem) {
+        cudaFuncSetAttribute(k_adj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        configured = smem;
+    }
+    k_adj_tc<<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, partial, spin, status);
+}
+
+// Sum the unit partials of each (channel, block) in unit order (FP64) into
+// gsum[c][N*N] (without the beam factor).
+__global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __restrict__ cb_unit_off,
+                                                       const float* __restrict__ partial,
+                                                       double* __restrict__ gsum) {
+    const int N = d.N;
+    const int64_t NN = (int64_t)N * N;
+    const int BLK = N < 256 ? N : 256;
+    const int nbx = N / BLK;
+    const int c = blockIdx.y;
+    const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (p >= NN) return;
+    const int n = (int)(p / N), m = (int)(p % N);
+    const int blk = (n / BLK) * nbx + m / BLK;
+    const int64_t loc = (int64_t)(n % BLK) * BLK + (m % BLK);
+    const int cb = c * nbx * nbx + blk;
+    double s = 0.0;
+    for (int u = cb_unit_off[cb]; u < cb_unit_off[cb + 1]; ++u) s += (double)partial[(int64_t)u * BLK * BLK + loc];
+    gsum[(int64_t)c * NN + p] = s;
+}
+
+void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* cb_unit_off,
+                          const float* partial, double* gsum, cudaStream_t st) {
+    (void)units;
+    dim3 grid(prep_blocks(d.N), d.C);
+    k_adj_tc_reduce<<<grid, 256, 0, st>>>(d, cb_unit_off, partial, gsum);
+}
+
+}  // namespace msk

@@ -1,0 +1,150 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+identical seeded inputs.
+
+Tolerances (stated for the split-precision tensor-core form; the direct FP64
+form must agree to rounding):
+  model visibilities   max|dV| / max|V|          <= 1e-5
+  gradient             ||dg||_2 / ||g||_2        <= 1e-4
+  objective            |dPhi| / |Phi|            <= 1e-6
+Sizes span several tiles (128 visibilities, 128/256-pixel blocks) and a ragged
+tail; cube cases include an empty channel.
+"""
+import numpy as np
+import pytest
+
+from paper_1703_02920_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+TOL_V = {"fp64_direct": 1e-10, "fp32_direct": 1e-5, "bf16x3": 1e-5}
+TOL_G = {"fp64_direct": 1e-10, "fp32_direct": 1e-4, "bf16x3": 1e-4}
+TOL_PHI = {"fp64_direct": 1e-11, "fp32_direct": 1e-6, "bf16x3": 1e-6}
+FORMS = ["fp64_direct", "fp32_direct", "bf16x3"]
+
+
+@pytest.fixture(scope="module")
+def ms():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1703_02920_gb300 import memsynth
+    memsynth.load()
+    return memsynth
+
+
+def _oracle_vis(oracle_mod, ds, img):
+    P = oracle_mod.Problem.from_dataset(ds)
+    return np.concatenate(oracle_mod.model_vis(P, np.asarray(img, dtype=np.float64)))
+
+
+def _rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+CASES = [
+    dict(N=64, Z=1000, C=1, shared=False, seed=1),
+    dict(N=128, Z=777, C=1, shared=False, seed=2),
+    dict(N=256, Z=300, C=1, shared=False, seed=3),
+    dict(N=64, Z=0, C=3, shared=False, seed=4, z_list=[257, 0, 130]),
+    dict(N=128, Z=0, C=3, shared=True, seed=5, z_list=[200, 129, 64]),
+]
+
+
+def _case(c):
+    return S.random_problem(c["N"], c["Z"], c["seed"], C=c["C"], shared_image=c["shared"],
+                            z_list=c.get("z_list"), lam=3.0)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ci", range(len(CASES)))
+def test_forward_parity(ms, oracle_mod, form, ci):
+    import torch
+    ds = _case(CASES[ci])
+    ctx = ms.Context(ds, precision=form)
+    img = ds.truth
+    V = ctx.forward(torch.from_numpy(img).cuda()).cpu().numpy().astype(np.float64)
+    ref = _oracle_vis(oracle_mod, ds, img)
+    got = V[:, 0] + 1j * V[:, 1]
+    assert _rel_max(got, ref) <= TOL_V[form]
+    ctx.close()
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ci", range(len(CASES)))
+def test_adjoint_parity(ms, oracle_mod, form, ci):
+    import torch
+    ds = _case(CASES[ci])
+    ctx = ms.Context(ds, precision=form)
+    y = S.random_complex(ds.Z, 100 + ci).astype(np.complex64)
+    yt = torch.from_numpy(np.stack([y.real, y.imag], 1)).cuda()
+    G = ctx.adjoint(yt).cpu().numpy().astype(np.float64)
+    P = oracle_mod.Problem.from_dataset(ds)
+    y64 = y.astype(np.complex128)
+    ref = np.zeros((P.n_images, P.N, P.N))
+    for c in range(P.C):
+        s = P.sl(c)
+        gc = P.pb[c] * oracle_mod.adjoint(P.N, P.dx, P.dy, P.u[s], P.v[s], y64[s])
+        ref[0 if P.shared_image else c] += gc
+    assert _rel_l2(G, ref) <= TOL_G[form]
+    ctx.close()
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ci", range(len(CASES)))
+def test_objective_gradient_parity(ms, oracle_mod, form, ci):
+    import torch
+    ds = _case(CASES[ci])
+    ctx = ms.Context(ds, precision=form)
+    img = ds.truth
+    phi, chi, Sv, g = ctx.objective_grad(torch.from_numpy(img).cuda())
+    P = oracle_mod.Problem.from_dataset(ds)
+    rphi, rchi, rS, rg = oracle_mod.objective_grad(P, img.astype(np.float64))
+    assert abs(phi - rphi) <= TOL_PHI[form] * abs(rphi)
+    assert abs(chi - rchi) <= TOL_PHI[form] * abs(rchi)
+    assert abs(Sv - rS) <= 1e-12 * abs(rS)
+    assert _rel_l2(g.cpu().numpy().astype(np.float64), rg) <= TOL_G[form]
+    # projected gradient: the bound rule applied on the device
+    _, _, _, gp = ctx.objective_grad(torch.from_numpy(img).cuda(), projected=True)
+    rgp = oracle_mod.project_grad(img.astype(np.float64), rg, P.G)
+    assert _rel_l2(gp.cpu().numpy().astype(np.float64), rgp) <= TOL_G[form]
+    ctx.close()
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_host_buffer_entry_matches_device_entry(ms, form):
+    import torch
+    ds = _case(CASES[0])
+    ctx = ms.Context(ds, precision=form)
+    a = ctx.objective_grad(torch.from_numpy(ds.truth).cuda())
+    b = ctx.objective_grad_host(ds.truth)
+    assert a[:3] == b[:3]
+    assert np.array_equal(a[3].cpu().numpy(), b[3])
+    ctx.close()
+
+
+def test_precision_switch_reuses_context(ms, oracle_mod):
+    import torch
+    ds = _case(CASES[1])
+    ctx = ms.Context(ds, precision="fp64_direct")
+    ref = _oracle_vis(oracle_mod, ds, ds.truth)
+    for form in ["bf16x3", "fp32_direct", "fp64_direct", "bf16x3"]:
+        ctx.set_precision(form)
+        V = ctx.forward(torch.from_numpy(ds.truth).cuda()).cpu().numpy().astype(np.float64)
+        assert _rel_max(V[:, 0] + 1j * V[:, 1], ref) <= TOL_V[form]
+    ctx.close()
+
+
+def test_deterministic_repeat(ms):
+    """Fixed-order reductions: two evaluations are bitwise identical."""
+    import torch
+    ds = _case(CASES[2])
+    ctx = ms.Context(ds, precision="bf16x3")
+    img = torch.from_numpy(ds.truth).cuda()
+    a = ctx.objective_grad(img)
+    b = ctx.objective_grad(img)
+    assert a[:3] == b[:3] and torch.equal(a[3], b[3])
+    ctx.close()
