@@ -67,6 +67,7 @@ class ClockSampler:
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        time.sleep(1.0)  # let the sampler start before the timed region
         return self
 
     def __exit__(self, *a):
@@ -162,7 +163,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 5])
@@ -240,7 +241,7 @@ def main():
     for _ in range(2):
         ctx.objective_grad_host(himg)
     e2e_ms = []
-    for _ in range(max(3, args.steps // 2)):
+    for _ in range(max(3, min(50, args.steps // 2))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -355,8 +355,20 @@ __global__ void __launch_bounds__(256) k_scalars_image(DevData d, const int* __r
     int c_lo = d.shared ? 0 : i, c_hi = d.shared ? d.C : i + 1;
     double chi = 0.0;
     for (int c = c_lo; c < c_hi; ++c) {
+        // thread t sums a contiguous run of partials (fixed order), 8 loads in flight
+        const int64_t t0 = 4LL * tile_off[c], t1 = 4LL * tile_off[c + 1];
+        const int64_t per = (t1 - t0 + 255) / 256;
+        const int64_t a = t0 + per * threadIdx.x, b = a + per < t1 ? a + per : t1;
         double part = 0.0;
-        for (int64_t t = 4LL * tile_off[c] + threadIdx.x; t < 4LL * tile_off[c + 1]; t += 256) part += chi_part[t];
+        int64_t t = a;
+        for (; t + 8 <= b; t += 8) {
+            double q[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) q[k] = chi_part[t + k];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) part += q[k];
+        }
+        for (; t < b; ++t) part += chi_part[t];
         double s = block_sum<256>(part, sh);
         if (threadIdx.x == 0) chi += s;
     }

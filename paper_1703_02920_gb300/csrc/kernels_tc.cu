@@ -605,8 +605,20 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __r
     const int blk = (n / BLK) * nbx + m / BLK;
     const int64_t loc = (int64_t)(n % BLK) * BLK + (m % BLK);
     const int cb = c * nbx * nbx + blk;
+    const int u0 = cb_unit_off[cb], u1 = cb_unit_off[cb + 1];
+    const int64_t stride = (int64_t)BLK * BLK;
+    const float* src = partial + loc;
     double s = 0.0;
-    for (int u = cb_unit_off[cb]; u < cb_unit_off[cb + 1]; ++u) s += (double)partial[(int64_t)u * BLK * BLK + loc];
+    int u = u0;
+    // eight independent loads in flight, added in unit order
+    for (; u + 8 <= u1; u += 8) {
+        float q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = __ldg(src + (int64_t)(u + k) * stride);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += (double)q[k];
+    }
+    for (; u < u1; ++u) s += (double)__ldg(src + (int64_t)u * stride);
     gsum[(int64_t)c * NN + p] = s;
 }
 

@@ -2,7 +2,7 @@
 identical seeded inputs.
 
 Tolerances (stated for the split-precision tensor-core form; the direct FP64
-form must agree to rounding):
+form agrees to the float32 rounding of the ABI's outputs):
   model visibilities   max|dV| / max|V|          <= 1e-5
   gradient             ||dg||_2 / ||g||_2        <= 1e-4
   objective            |dPhi| / |Phi|            <= 1e-6
@@ -16,8 +16,10 @@ from paper_1703_02920_gb300 import synth as S
 
 pytestmark = pytest.mark.gpu
 
-TOL_V = {"fp64_direct": 1e-10, "fp32_direct": 1e-5, "bf16x3": 1e-5}
-TOL_G = {"fp64_direct": 1e-10, "fp32_direct": 1e-4, "bf16x3": 1e-4}
+# The FP64 form computes in FP64 but returns visibilities and gradients as
+# float32 through the ABI, so it agrees to float32 rounding of its outputs.
+TOL_V = {"fp64_direct": 2e-7, "fp32_direct": 1e-5, "bf16x3": 1e-5}
+TOL_G = {"fp64_direct": 2e-7, "fp32_direct": 1e-4, "bf16x3": 1e-4}
 TOL_PHI = {"fp64_direct": 1e-11, "fp32_direct": 1e-6, "bf16x3": 1e-6}
 FORMS = ["fp64_direct", "fp32_direct", "bf16x3"]
 
