@@ -30,19 +30,26 @@ constexpr int LS_MAX_EVALS = 20;              // objective evaluations per line 
 constexpr double LS_TOL = 1e-3;               // relative step tolerance (Brent)
 constexpr double LS_EPS = 1e-10;              // absolute tolerance / first trial step
 constexpr int RESTART = 50;                   // steepest-descent restart period
+constexpr double POLISH = 0.2;                // half-width of the final 3-point Newton step / step
 
 // Line search on phi(alpha), alpha >= 0, as a resumable state machine so that
 // many images (cube channels) can share each batched objective evaluation.
 // Bracketing: shrink the trial step until phi < phi(0), or expand it by GOLD
-// while phi keeps falling; then Brent's method (Brent 1973, ch. 5).
+// while phi keeps falling; then Brent's method (Brent 1973, ch. 5); then one
+// Newton step on central differences over x -/+ h, h = min(POLISH alpha0,
+// x / 2), clamped to that interval.  Brent stops anywhere inside its tolerance; the last step moves
+// the result to within O(tol^2) of the minimiser by a formula continuous in
+// the objective values, so different roundings give the same step.
 struct LineSearch {
-    enum Phase { INIT, SHRINK_P, EXPAND, BRENT, DONE } phase = DONE;
+    enum Phase { INIT, SHRINK_P, EXPAND, BRENT, POL_P, POL_M, DONE } phase = DONE;
+    double px = 0, pfx = 0, ph = 0, pfp = 0;
     int evals = 0, nb = 0, budget = 0;
-    double f0 = 0, a = 0, fa = 0, b = 0, fb = 0, c = 0, fc = 0, eps = 0;
+    double f0 = 0, a = 0, fa = 0, b = 0, fb = 0, c = 0, fc = 0, eps = 0, a0 = 0;
     double lo = 0, hi = 0, x = 0, w = 0, v = 0, fx = 0, fw = 0, fv = 0, d = 0, e = 0;
     double req = 0, alpha = 0, falpha = 0;
 
     void start(double phi0, double alpha0) {
+        a0 = alpha0;
         f0 = phi0;
         eps = LS_EPS * alpha0;
         a = 0.0;
@@ -54,6 +61,14 @@ struct LineSearch {
     }
     bool running() const { return phase != DONE; }
     void finish(double al, double f) {
+        if (al > 0.0) {
+            px = al;
+            pfx = f;
+            ph = std::min(POLISH * a0, 0.5 * al);
+            req = px + ph;
+            phase = POL_P;
+            return;
+        }
         alpha = al;
         falpha = f;
         phase = DONE;
@@ -185,6 +200,25 @@ struct LineSearch {
                     }
                 }
                 brent_step();
+                break;
+            }
+            case POL_P:
+                pfp = f;
+                evals += 1;
+                req = px - ph;
+                phase = POL_M;
+                break;
+            case POL_M: {
+                const double fm = f;
+                evals += 1;
+                double x = px;
+                const double curv = pfp - 2.0 * pfx + fm;
+                if (curv > 0.0) {
+                    const double t = px - ph * (pfp - fm) / (2.0 * curv);
+                    x = std::min(std::max(t, px - ph), px + ph);
+                }
+                alpha = x;
+                phase = DONE;
                 break;
             }
             case DONE:
@@ -781,7 +815,7 @@ mem_status mem_forward(mem_ctx* c, const float* image_dev, float* vis_dev) {
     if (!c || !image_dev || (!vis_dev && c->Z > 0)) return fail(c, MEM_EINVAL, "null argument");
     if (!aligned(vis_dev, 8)) return fail(c, MEM_EINVAL, "vis_dev must be 8-byte aligned");
     TRY(ensure_buffers(c));
-    ImgSrc src{image_dev, nullptr, nullptr, nullptr, c->G};
+    ImgSrc src{image_dev, nullptr, nullptr, nullptr, c->G, 0};
     if (c->prec == MEM_PREC_FP64_DIRECT) {
         TRY(run_forward(c, src, FWD_VIS, false, c->y64));
         launch_f64_to_f32(2 * c->Z, (const double*)c->y64, vis_dev, c->st);
@@ -816,7 +850,7 @@ mem_status mem_adjoint(mem_ctx* c, const float* y_dev, float* img_dev) {
     // beam factor and channel sum only: lambda = 0 view of the assembly
     DevData d = c->dd();
     d.lambda = 0.0;
-    ImgSrc src{nullptr, nullptr, nullptr, nullptr, c->G};
+    ImgSrc src{nullptr, nullptr, nullptr, nullptr, c->G, 0};
     // the assembly reads pixel values only for the entropy term and projection;
     // give it the output buffer as a harmless source (lambda = 0, no projection)
     src.f32 = img_dev;
@@ -828,7 +862,7 @@ mem_status mem_adjoint(mem_ctx* c, const float* y_dev, float* img_dev) {
 mem_status mem_objective_grad(mem_ctx* c, const float* image_dev, float* grad_dev, int32_t projected,
                               double* out3_host) {
     if (!c || !image_dev) return fail(c, MEM_EINVAL, "null argument");
-    ImgSrc src{image_dev, nullptr, nullptr, nullptr, c->G};
+    ImgSrc src{image_dev, nullptr, nullptr, nullptr, c->G, 0};
     TRY(run_objgrad(c, src, projected, grad_dev, nullptr, nullptr));
     if (out3_host) {
         std::vector<double> sc;
@@ -886,7 +920,7 @@ mem_status mem_solve(mem_ctx* c, float* image_dev_inout, int32_t n_iter, mem_sol
     int stopped_early = 0;
 
     auto objgrad = [&]() -> mem_status {
-        ImgSrc src{nullptr, c->I64, nullptr, nullptr, c->G};
+        ImgSrc src{nullptr, c->I64, nullptr, nullptr, c->G, 0};
         TRY(run_objgrad(c, src, 1, nullptr, c->gf64, c->g64));
         TRY(read_scalars(c, sc));
         for (int i = 0; i < NI; ++i) {
@@ -968,7 +1002,7 @@ mem_status mem_solve(mem_ctx* c, float* image_dev_inout, int32_t n_iter, mem_sol
             }
         // quadratic model of chi^2 along d: curvature sum w |F(A d)|^2
         {
-            ImgSrc src{nullptr, c->d64, nullptr, nullptr, c->G};
+            ImgSrc src{nullptr, c->d64, nullptr, nullptr, c->G, 0};
             TRY(run_forward(c, src, FWD_CURV, false, nullptr));
             TRY(read_scalars(c, sc));
         }
@@ -997,11 +1031,15 @@ mem_status mem_solve(mem_ctx* c, float* image_dev_inout, int32_t n_iter, mem_sol
             }
             if (!running) break;
             TRY(set_dev(c->alpha, alpha.data(), NI * sizeof(double)));
-            ImgSrc src{nullptr, c->I64, c->d64, c->alpha, c->G};
-            TRY(run_forward(c, src, FWD_CHI, true, nullptr));
+            // phi(alpha) = Phi(I) + [Phi(max(I + alpha d, G)) - Phi(I)], the change
+            // evaluated from the image difference so that its rounding error
+            // scales with the step, not with Phi
+            ImgSrc src{nullptr, c->I64, c->d64, c->alpha, c->G, 1};
+            void* ybuf = c->prec == MEM_PREC_FP64_DIRECT ? (void*)c->y64 : (void*)c->y32;
+            TRY(run_forward(c, src, FWD_DCHI, true, ybuf));
             TRY(read_scalars(c, sc));
             for (int i = 0; i < NI; ++i)
-                if (active[i] && ls[i].running()) ls[i].feed(sc[3 + 3 * i]);
+                if (active[i] && ls[i].running()) ls[i].feed(phi[i] + sc[3 + 3 * i]);
         }
         for (int i = 0; i < NI; ++i) {
             alpha[i] = 0.0;

@@ -51,10 +51,16 @@ struct ImgSrc {
     const double* dir;
     const double* alpha;  // per image (device)
     double G;
+    int diff;             // operand is max(I + alpha d, G) - I, entropy as a difference
 };
 
 enum BFormat { BF_F32 = 0, BF_F64 = 1, BF_BF16X3 = 2 };
-enum FwdMode { FWD_VIS = 0, FWD_RESID = 1, FWD_CHI = 2, FWD_CURV = 3 };
+// FWD_VIS: write V.  FWD_RESID: write y = w (V - V^o), chi^2 partials.
+// FWD_CHI: chi^2 partials only.  FWD_CURV: 1/2 w |V|^2 partials.
+// FWD_DCHI: chi^2 change for an operand that is an image difference delta,
+//   Re(conj(y) F(A delta)) + 1/2 w |F(A delta)|^2, with y = w r of the base
+//   image read from the y buffer.
+enum FwdMode { FWD_VIS = 0, FWD_RESID = 1, FWD_CHI = 2, FWD_CURV = 3, FWD_DCHI = 4 };
 
 // Forward tensor-core tiling: m-block width and n per pipeline stage.
 constexpr int TC_BK = 32;

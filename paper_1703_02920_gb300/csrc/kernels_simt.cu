@@ -106,7 +106,18 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
     double e = 0.0;
     if (p < NN) {
         double x = img_value(src, i, p, NN);
-        double b = (double)d.beam[(int64_t)c * NN + p] * x;
+        double xb = x;
+        if (src.diff) {
+            // line-search probe as a difference from the base image I: the
+            // operand is delta = max(I + alpha d, G) - I, the entropy term the
+            // change of sum x log(x/G)
+            const double x0 = src.f64[(int64_t)i * NN + p];
+            xb = x - x0;
+            if (ent_part) e = x * log(x / src.G) - x0 * log(x0 / src.G);
+        } else if (ent_part) {
+            e = x * log(x / src.G);
+        }
+        double b = (double)d.beam[(int64_t)c * NN + p] * xb;
         if (fmt == BF_F32) {
             ((float*)bout)[(int64_t)c * NN + p] = (float)b;
         } else if (fmt == BF_F64) {
@@ -122,7 +133,6 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
             base[q] = hi;
             base[q + (int64_t)BN * TC_BK] = lo;
         }
-        if (ent_part) e = x * log(x / src.G);
     }
     if (ent_part) {
         bool owner = d.shared ? (c == 0) : true;
@@ -194,6 +204,11 @@ __global__ void __launch_bounds__(128) k_fwd_direct(DevData d, const VisTile* __
         if (mode == FWD_VIS) {
             if (sizeof(T) == 8) ((double2*)yout)[j] = make_double2(re, im);
             else ((float2*)yout)[j] = make_float2((float)re, (float)im);
+        } else if (mode == FWD_DCHI) {
+            double yr, yi;
+            if (sizeof(T) == 8) { double2 q = ((const double2*)yout)[j]; yr = q.x; yi = q.y; }
+            else { float2 q = ((const float2*)yout)[j]; yr = q.x; yi = q.y; }
+            chi = yr * re + yi * im + 0.5 * d.w[j] * (re * re + im * im);
         } else {
             double rr = re, ri = im;
             if (mode != FWD_CURV) { rr -= d.vo[j].x; ri -= d.vo[j].y; }

@@ -274,6 +274,9 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
             if (valid) {
                 if (mode == FWD_VIS) {
                     yout[j] = make_float2((float)vre, (float)vim);
+                } else if (mode == FWD_DCHI) {
+                    const float2 q = yout[j];
+                    chi = (double)q.x * vre + (double)q.y * vim + 0.5 * d.w[j] * (vre * vre + vim * vim);
                 } else {
                     double rr = vre, ri = vim;
                     if (mode != FWD_CURV) { rr -= d.vo[j].x; ri -= d.vo[j].y; }

@@ -57,10 +57,11 @@ def test_cube_solve_batched_equals_oracle_per_channel(ms, oracle_mod):
     import torch
     ds = S.random_problem(64, 0, seed=31, C=3, z_list=[400, 0, 257], lam=20.0, G=1e-3)
     P = oracle_mod.Problem.from_dataset(ds)
-    I0 = np.full((3, 64, 64), P.G)
-    ref, hists = oracle_mod.solve(P, I0, 8)
+    # the same float32 start on both sides (float32(1e-3) lies just above G)
+    I0 = np.full((3, 64, 64), P.G).astype(np.float32)
+    ref, hists = oracle_mod.solve(P, I0.astype(np.float64), 8)
     ctx = ms.Context(ds, precision="fp64_direct")
-    img, rep, hist = ctx.solve(torch.from_numpy(I0.astype(np.float32)).cuda(), 8)
+    img, rep, hist = ctx.solve(torch.from_numpy(I0).cuda(), 8)
     img = img.cpu().numpy().astype(np.float64)
     for c in range(3):
         rel = np.linalg.norm(img[c] - ref[c]) / np.linalg.norm(ref[c])
