@@ -311,6 +311,8 @@ struct mem_ctx {
         d.w = w;
         d.beam = beam;
         d.off = doff;
+        d.dx = dx;
+        d.dy = dy;
         return d;
     }
 };
@@ -491,7 +493,7 @@ mem_status ensure_buffers(mem_ctx* c) {
     TRY(dalloc(c, &c->chi_part, (size_t)4 * std::max(c->n_tiles, 1)));
     TRY(dalloc(c, &c->ent_part, (size_t)c->n_images * prep_blocks(c->N)));
     TRY(dalloc(c, &c->scal, (size_t)3 + 3 * c->n_images));
-    TRY(dalloc(c, &c->img_tmp, (size_t)3 * c->n_images));
+    TRY(dalloc(c, &c->img_tmp, (size_t)scalars_tmp_doubles(c->n_images)));
     TRY(dalloc(c, &c->y32, (size_t)std::max<int64_t>(c->Z, 1)));
     if (c->prec == MEM_PREC_FP64_DIRECT) {
         TRY(dalloc(c, &c->y64, (size_t)std::max<int64_t>(c->Z, 1)));

@@ -24,6 +24,13 @@ __host__ __device__ __forceinline__ uint64_t phase_mul(int64_t k, uint64_t a) {
     return (uint64_t)k * a;
 }
 
+// frac(t) as a 64-bit fixed-point fraction of a turn (FP64 reduction).
+__device__ __forceinline__ uint64_t to_fixed_turns(double t) {
+    double f = t - rint(t);  // [-0.5, 0.5]
+    if (f >= 0.5) f -= 1.0;  // same turn, keeps f * 2^64 inside int64
+    return (uint64_t)__double2ll_rn(f * 18446744073709551616.0);
+}
+
 // Angle in radians in [-pi, pi) from the top 32 bits of a fixed-point phase.
 __device__ __forceinline__ float phase_to_angle_f32(uint64_t p) {
     const float k2pi_2m32 = 6.283185307179586f / 4294967296.0f;
@@ -33,6 +40,14 @@ __device__ __forceinline__ float phase_to_angle_f32(uint64_t p) {
 // Turns in [-0.5, 0.5) as FP64 from all 64 bits.
 __device__ __forceinline__ double phase_to_turns_f64(uint64_t p) {
     return (double)(int64_t)p * 5.421010862427522e-20;  // 2^-64
+}
+
+// Compensated accumulation (Neumaier): s + c carries the sum of the added
+// terms to about twice FP32 precision, in a fixed order.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
 }
 
 // exp(-i * angle) components for the forward sign convention are (c, -s).

@@ -41,6 +41,7 @@ struct DevData {
     const double* w;     // 1/sigma^2
     const float* beam;   // C*N*N
     const int64_t* off;  // C+1
+    double dx, dy;       // pixel size (radians)
 };
 
 // Where pixel values come from: the caller's FP32 image, or the solver's FP64
@@ -108,6 +109,7 @@ void launch_finalize(const DevData& d, const ImgSrc& src, const double* gsum, in
 void launch_scalars(const DevData& d, const int* tile_off, const double* chi_part,
                     const double* ent_part, int with_entropy, double* scal, double* img_tmp,
                     cudaStream_t st);
+int scalars_tmp_doubles(int n_images);
 
 // Solver vector kernels (FP64, per image).
 void launch_dots(const DevData& d, int which, const double* a, const double* b, const double* c,

@@ -16,12 +16,6 @@ namespace msk {
 // a 64-bit fixed-point fraction of a turn; pixel phases are then exact integer
 // multiples (Eq. 1 on the grid x_m = (m - N/2) dx).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t to_fixed_turns(double t) {
-    double f = t - rint(t);       // [-0.5, 0.5]
-    if (f >= 0.5) f -= 1.0;       // same turn, keeps f * 2^64 inside int64
-    return (uint64_t)__double2ll_rn(f * 18446744073709551616.0);
-}
-
 __global__ void k_phase_prep(int64_t Z, const double* __restrict__ u, const double* __restrict__ v,
                              double dx, double dy, uint64_t* __restrict__ pa,
                              uint64_t* __restrict__ pb) {
@@ -360,69 +354,79 @@ void launch_finalize(const DevData& d, const ImgSrc& src, const double* gsum, in
 // Ordered FP64 reductions of tile partials into per-image and total scalars.
 // scal layout: [0..2] = Phi, chi^2, S totals; [3 + 3i ...] per image.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scalars_image(DevData d, const int* __restrict__ tile_off,
-                                                       const double* __restrict__ chi_part,
-                                                       const double* __restrict__ ent_part,
-                                                       int with_entropy, int n_ent_blocks,
-                                                       double* __restrict__ img_tmp) {
+// Stage 1: grid (images, SCAL_SPLIT); block (i, q) sums a contiguous share of
+// image i's chi^2 partials and entropy partials in a fixed order.
+constexpr int SCAL_SPLIT = 32;
+
+__global__ void __launch_bounds__(256) k_scalars_part(DevData d, const int* __restrict__ tile_off,
+                                                      const double* __restrict__ chi_part,
+                                                      const double* __restrict__ ent_part,
+                                                      int with_entropy, int n_ent_blocks,
+                                                      double* __restrict__ part) {
     __shared__ double sh[8];
-    const int i = blockIdx.x;
+    const int i = blockIdx.x, q = blockIdx.y;
     int c_lo = d.shared ? 0 : i, c_hi = d.shared ? d.C : i + 1;
-    double chi = 0.0;
-    for (int c = c_lo; c < c_hi; ++c) {
-        // thread t sums a contiguous run of partials (fixed order), 8 loads in flight
-        const int64_t t0 = 4LL * tile_off[c], t1 = 4LL * tile_off[c + 1];
-        const int64_t per = (t1 - t0 + 255) / 256;
-        const int64_t a = t0 + per * threadIdx.x, b = a + per < t1 ? a + per : t1;
-        double part = 0.0;
-        int64_t t = a;
-        for (; t + 8 <= b; t += 8) {
-            double q[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) q[k] = chi_part[t + k];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) part += q[k];
-        }
-        for (; t < b; ++t) part += chi_part[t];
-        double s = block_sum<256>(part, sh);
-        if (threadIdx.x == 0) chi += s;
-    }
+    const int64_t t0 = 4LL * tile_off[c_lo], t1 = 4LL * tile_off[c_hi];  // channels are contiguous
+    const int64_t len = t1 - t0;
+    const int64_t a = t0 + len * q / SCAL_SPLIT, b = t0 + len * (q + 1) / SCAL_SPLIT;
+    double x = 0.0;
+    for (int64_t t = a + threadIdx.x; t < b; t += 256) x += chi_part[t];
+    const double chi = block_sum<256>(x, sh);
     double S = 0.0;
     if (with_entropy) {
-        double part = 0.0;
-        for (int b = threadIdx.x; b < n_ent_blocks; b += 256) part += ent_part[(int64_t)i * n_ent_blocks + b];
-        S = block_sum<256>(part, sh);
+        const int e0 = (int)((int64_t)n_ent_blocks * q / SCAL_SPLIT), e1 = (int)((int64_t)n_ent_blocks * (q + 1) / SCAL_SPLIT);
+        double y = 0.0;
+        for (int e = e0 + threadIdx.x; e < e1; e += 256) y += ent_part[(int64_t)i * n_ent_blocks + e];
+        S = block_sum<256>(y, sh);
     }
     if (threadIdx.x == 0) {
-        img_tmp[3 * i + 0] = chi - d.lambda * S;
-        img_tmp[3 * i + 1] = chi;
-        img_tmp[3 * i + 2] = S;
+        part[((int64_t)i * SCAL_SPLIT + q) * 2] = chi;
+        part[((int64_t)i * SCAL_SPLIT + q) * 2 + 1] = S;
     }
 }
 
-__global__ void k_scalars_total(int n_images, const double* __restrict__ img_tmp, double* scal) {
-    if (threadIdx.x != 0) return;
-    double a = 0, b = 0, c = 0;
-    for (int i = 0; i < n_images; ++i) {
-        a += img_tmp[3 * i];
-        b += img_tmp[3 * i + 1];
-        c += img_tmp[3 * i + 2];
-        scal[3 + 3 * i] = img_tmp[3 * i];
-        scal[4 + 3 * i] = img_tmp[3 * i + 1];
-        scal[5 + 3 * i] = img_tmp[3 * i + 2];
+// Stage 2: one thread per image sums its SCAL_SPLIT partials in order; thread
+// 0 then forms the totals in image order.
+__global__ void k_scalars_total(int n_images, double lambda, const double* __restrict__ part,
+                                double* img_tmp, double* scal) {
+    for (int i = threadIdx.x; i < n_images; i += blockDim.x) {
+        double chi = 0.0, S = 0.0;
+        for (int q = 0; q < SCAL_SPLIT; ++q) {
+            chi += part[((int64_t)i * SCAL_SPLIT + q) * 2];
+            S += part[((int64_t)i * SCAL_SPLIT + q) * 2 + 1];
+        }
+        img_tmp[3 * i] = chi - lambda * S;
+        img_tmp[3 * i + 1] = chi;
+        img_tmp[3 * i + 2] = S;
+        scal[3 + 3 * i] = chi - lambda * S;
+        scal[4 + 3 * i] = chi;
+        scal[5 + 3 * i] = S;
     }
-    scal[0] = a;
-    scal[1] = b;
-    scal[2] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0;
+        for (int i = 0; i < n_images; ++i) {
+            a += img_tmp[3 * i];
+            b += img_tmp[3 * i + 1];
+            c += img_tmp[3 * i + 2];
+        }
+        scal[0] = a;
+        scal[1] = b;
+        scal[2] = c;
+    }
 }
 
 void launch_scalars(const DevData& d, const int* tile_off, const double* chi_part,
                     const double* ent_part, int with_entropy, double* scal, double* img_tmp,
                     cudaStream_t st) {
-    k_scalars_image<<<d.n_images, 256, 0, st>>>(d, tile_off, chi_part, ent_part, with_entropy,
-                                                prep_blocks(d.N), img_tmp);
-    k_scalars_total<<<1, 32, 0, st>>>(d.n_images, img_tmp, scal);
+    // img_tmp holds 3 * n_images + 2 * SCAL_SPLIT * n_images doubles
+    double* part = img_tmp + 3 * d.n_images;
+    k_scalars_part<<<dim3(d.n_images, SCAL_SPLIT), 256, 0, st>>>(d, tile_off, chi_part, ent_part,
+                                                                  with_entropy, prep_blocks(d.N), part);
+    k_scalars_total<<<1, 256, 0, st>>>(d.n_images, d.lambda, part, img_tmp, scal);
 }
+
+int scalars_tmp_doubles(int n_images) { return 3 * n_images + 2 * 32 * n_images; }
 
 // ---------------------------------------------------------------------------
 // a8: CG vector kernels (FP64), per image.

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
             cf2 step[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) step[q] = cis_neg(phase_mul(q, pa));
-            double vre = 0.0, vim = 0.0;
+            float vre = 0.f, vim = 0.f, cre = 0.f, cim = 0.f;  // compensated sums
             for (int mb = 0; mb < n_mb; ++mb, ++it) {
                 const int b = it & 1;
                 ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull[b], (it >> 1) & 1, spin, abort, status));
@@ -262,8 +262,8 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
                         ar = fmaf(ex.x, tr, fmaf(-ex.y, ti, ar));
                         ai = fmaf(ex.x, ti, fmaf(ex.y, tr, ai));
                     }
-                    vre += (double)ar;
-                    vim += (double)ai;
+                    two_sum_acc(vre, cre, ar);
+                    two_sum_acc(vim, cim, ai);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -272,13 +272,14 @@ __global__ void __launch_bounds__(FWD_THREADS, 1)
             if (!ok) break;
             double chi = 0.0;
             if (valid) {
+                const double Vre = (double)vre + (double)cre, Vim = (double)vim + (double)cim;
                 if (mode == FWD_VIS) {
-                    yout[j] = make_float2((float)vre, (float)vim);
+                    yout[j] = make_float2((float)Vre, (float)Vim);
                 } else if (mode == FWD_DCHI) {
                     const float2 q = yout[j];
-                    chi = (double)q.x * vre + (double)q.y * vim + 0.5 * d.w[j] * (vre * vre + vim * vim);
+                    chi = (double)q.x * Vre + (double)q.y * Vim + 0.5 * d.w[j] * (Vre * Vre + Vim * Vim);
                 } else {
-                    double rr = vre, ri = vim;
+                    double rr = Vre, ri = Vim;
                     if (mode != FWD_CURV) { rr -= d.vo[j].x; ri -= d.vo[j].y; }
                     const double w = d.w[j];
                     chi = 0.5 * w * (rr * rr + ri * ri);
@@ -584,11 +585,7 @@ void launch_adj_tc(const DevData& d, const AdjUnit* units, const int* cta_unit_o
                    const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st) {
     if (n_ctas <= 0) return;
     int smem = adj_tc_smem_bytes(d.N);
-    static int configured = 0;
-    if (configured < smem) {
-        cudaFuncSetAttribute(k_adj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        configured = smem;
-    }
+    cudaFuncSetAttribute(k_adj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_adj_tc<<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, partial, spin, status);
 }
 
@@ -611,18 +608,19 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __r
     const int u0 = cb_unit_off[cb], u1 = cb_unit_off[cb + 1];
     const int64_t stride = (int64_t)BLK * BLK;
     const float* src = partial + loc;
-    double s = 0.0;
+    // compensated FP32 sum in unit order (Neumaier); FP64 throughput on this
+    // part is too low for one FP64 add per partial
+    float s = 0.f, comp = 0.f;
     int u = u0;
-    // eight independent loads in flight, added in unit order
     for (; u + 8 <= u1; u += 8) {
         float q[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) q[k] = __ldg(src + (int64_t)(u + k) * stride);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) s += (double)q[k];
+        for (int k = 0; k < 8; ++k) two_sum_acc(s, comp, q[k]);
     }
-    for (; u < u1; ++u) s += (double)__ldg(src + (int64_t)u * stride);
-    gsum[(int64_t)c * NN + p] = s;
+    for (; u < u1; ++u) two_sum_acc(s, comp, __ldg(src + (int64_t)u * stride));
+    gsum[(int64_t)c * NN + p] = (double)s + (double)comp;
 }
 
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* cb_unit_off,
