@@ -178,6 +178,35 @@ mem_status mem_profile(mem_ctx *ctx, int32_t enable);
 int32_t mem_profile_read(mem_ctx *ctx, int32_t max_kernels, char *names, double *ms_total,
                          int64_t *launches);
 
+/* Adjoint without device allocation (no counterpart in the paper).
+ *
+ * For callers that cannot allocate device memory: code running inside a
+ * framework that owns all device memory through its own pool or arena and
+ * forbids side allocations, or code that must not allocate after start-up.
+ * They keep their inputs and outputs in device memory themselves; this call
+ * needs nothing else and calls no cudaMalloc / cudaFree or allocating library
+ * routine.
+ *
+ * Computes, for one channel with the split-BF16 tensor-core form,
+ *   img_dev[n*N + m] = pb_dev[n*N + m] * sum_k Re( y_k exp(+2 pi i (u_k x_m + v_k y_n)) )
+ * (the same operation as mem_adjoint).  All pointers are device pointers:
+ * u_dev, v_dev (n_vis doubles, wavelengths), y_dev (2*n_vis floats, re/im,
+ * 8-byte aligned), pb_dev and img_dev (N*N floats).  N must be 64, 128 or
+ * 256; other sizes return MEM_EINVAL with a message in mem_last_error(NULL).
+ *
+ * Scratch lives in a fixed static device array of about 16 MB (split-K
+ * partials for at most 64 CTAs plus the work list) that every GPU loading the
+ * library holds until exit.  All calls share it: calls that overlap on the
+ * GPU race and must be serialised by the caller.  The array keeps the last
+ * call's contents; nothing in it needs clearing between calls.  The first
+ * call on a device resolves the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * The call is synchronous on `stream` (it reads back a device status word)
+ * and returns MEM_ETIMEOUT if a bounded device-side wait ran out. */
+mem_status mem_adjoint_noalloc(int32_t n, double dx, double dy, int64_t n_vis,
+                               const double *u_dev, const double *v_dev, const float *y_dev,
+                               const float *pb_dev, float *img_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -610,6 +610,8 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 }  // namespace
 
+void msk::set_global_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 extern "C" {
 
 const char* mem_status_string(mem_status s) {

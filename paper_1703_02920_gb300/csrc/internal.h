@@ -70,6 +70,9 @@ inline int tc_bn(int N) { return N < 128 ? N : 128; }
 constexpr int TCA_BK = 16;
 inline int tca_blk(int N) { return N < 256 ? N : 256; }
 
+// Message returned by mem_last_error(NULL) (thread-local).
+void set_global_error(const char* msg);
+
 // ---- launchers (all asynchronous on `st`) ----
 void launch_phase_prep(int64_t Z, const double* u, const double* v, double dx, double dy,
                        uint64_t* pa, uint64_t* pb, cudaStream_t st);
@@ -96,6 +99,13 @@ int adj_tc_smem_bytes(int N);
 // units sorted by CTA: CTA b runs units [cta_unit_off[b], cta_unit_off[b+1]).
 void launch_adj_tc(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
                    const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st);
+// Variant reading u, v (FP64, wavelengths) instead of the prepared phase
+// increments: the caller passes d.u, d.v, d.dx, d.dy; d.pa / d.pb are unused.
+void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
+                      const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st);
+// out[p] = A[p] * sum of unit partials (single channel, unit order, FP64 sum).
+void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partial, const float* beam,
+                              float* out, cudaStream_t st);
 // Sum unit partials per channel (unit order) into gsum[C][N*N].
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* unit_off_by_chan_blk,
                           const float* partial, double* gsum, cudaStream_t st);

@@ -352,6 +352,9 @@ struct AdjShared {
     int abort;
 };
 
+// FROM_UV: phase increments reduced from u, v inside the producers instead of
+// read from the prepared arrays.
+template <bool FROM_UV>
 __global__ void __launch_bounds__(ADJ_THREADS, 1)
     k_adj_tc(DevData d, const AdjUnit* __restrict__ units, const int* __restrict__ cta_unit_off,
              const float2* __restrict__ y, float* __restrict__ partial, uint64_t spin, int* status) {
@@ -460,8 +463,13 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                 uint64_t pa = 0, pb = 0;
                 cf2 yv = {0.f, 0.f};
                 if (valid) {
-                    pa = d.pa[un.start + kv];
-                    pb = d.pb[un.start + kv];
+                    if (FROM_UV) {
+                        pa = to_fixed_turns(d.u[un.start + kv] * d.dx);
+                        pb = to_fixed_turns(d.v[un.start + kv] * d.dy);
+                    } else {
+                        pa = d.pa[un.start + kv];
+                        pb = d.pb[un.start + kv];
+                    }
                     const float2 t = y[un.start + kv];
                     yv = {t.x, t.y};
                 }
@@ -585,8 +593,40 @@ void launch_adj_tc(const DevData& d, const AdjUnit* units, const int* cta_unit_o
                    const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st) {
     if (n_ctas <= 0) return;
     int smem = adj_tc_smem_bytes(d.N);
-    cudaFuncSetAttribute(k_adj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_adj_tc<<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, partial, spin, status);
+    cudaFuncSetAttribute(k_adj_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_adj_tc<false><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, partial, spin, status);
+}
+
+void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
+                      const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st) {
+    if (n_ctas <= 0) return;
+    int smem = adj_tc_smem_bytes(d.N);
+    cudaFuncSetAttribute(k_adj_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_adj_tc<true><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, partial, spin, status);
+}
+
+// Single channel: out[p] = A[p] * (unit partials summed in unit order, FP64).
+__global__ void __launch_bounds__(256) k_adj_tc_reduce_out(int N, const int* __restrict__ cb_unit_off,
+                                                           const float* __restrict__ partial,
+                                                           const float* __restrict__ beam,
+                                                           float* __restrict__ out) {
+    const int64_t NN = (int64_t)N * N;
+    const int BLK = N < 256 ? N : 256;
+    const int nbx = N / BLK;
+    const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (p >= NN) return;
+    const int n = (int)(p / N), m = (int)(p % N);
+    const int blk = (n / BLK) * nbx + m / BLK;
+    const int64_t loc = (int64_t)(n % BLK) * BLK + (m % BLK);
+    float s = 0.f, comp = 0.f;
+    for (int u = cb_unit_off[blk]; u < cb_unit_off[blk + 1]; ++u)
+        two_sum_acc(s, comp, __ldg(partial + (int64_t)u * BLK * BLK + loc));
+    out[p] = beam[p] * (s + comp);
+}
+
+void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partial, const float* beam,
+                              float* out, cudaStream_t st) {
+    k_adj_tc_reduce_out<<<prep_blocks(N), 256, 0, st>>>(N, cb_unit_off, partial, beam, out);
 }
 
 // Sum the unit partials of each (channel, block) in unit order (FP64) into
