@@ -256,12 +256,13 @@ struct mem_ctx {
     float* beam = nullptr;
     int64_t* doff = nullptr;
 
-    // work lists
-    std::vector<VisTile> tiles_h;
-    std::vector<int> tile_off_h;
-    VisTile* tiles = nullptr;
-    int* tile_off = nullptr;
-    int n_tiles = 0;
+    // work lists: visibility tiles for the direct forms (128) and the
+    // tensor-core form (TC_TILE)
+    std::vector<VisTile> tiles_h, tiles_tc_h;
+    std::vector<int> tile_off_h, tile_off_tc_h;
+    VisTile *tiles = nullptr, *tiles_tc = nullptr;
+    int *tile_off = nullptr, *tile_off_tc = nullptr;
+    int n_tiles = 0, n_tiles_tc = 0;
     std::vector<AdjUnit> units_h;
     std::vector<int> cta_off_h, cb_off_h;
     AdjUnit* units = nullptr;
@@ -276,6 +277,7 @@ struct mem_ctx {
     float* bf32 = nullptr;
     double* bf64 = nullptr;
     uint16_t* planes = nullptr;
+    float* cmean = nullptr;  // column means of the centred tensor-core operand
     float* partial = nullptr;
     int* dstatus = nullptr;
     float* stage = nullptr;  // host-call staging (image, gradient)
@@ -397,22 +399,21 @@ mem_status dalloc(mem_ctx* c, T** p, size_t count) {
 
 bool tc_shape_ok(int N) { return N == 64 || N == 128 || (N >= 256 && N % 256 == 0); }
 
-// 128-visibility tiles per channel, in channel order.
-void build_tiles(mem_ctx* c) {
-    c->tiles_h.clear();
-    c->tile_off_h.assign(c->C + 1, 0);
+// Visibility tiles of `size` per channel, in channel order.
+void build_tiles(const mem_ctx* c, int size, std::vector<VisTile>& tiles, std::vector<int>& off) {
+    tiles.clear();
+    off.assign(c->C + 1, 0);
     for (int ch = 0; ch < c->C; ++ch) {
-        c->tile_off_h[ch] = (int)c->tiles_h.size();
-        for (int64_t s = c->off[ch]; s < c->off[ch + 1]; s += 128) {
+        off[ch] = (int)tiles.size();
+        for (int64_t s = c->off[ch]; s < c->off[ch + 1]; s += size) {
             VisTile t;
             t.chan = ch;
             t.start = s;
-            t.count = (int)std::min<int64_t>(128, c->off[ch + 1] - s);
-            c->tiles_h.push_back(t);
+            t.count = (int)std::min<int64_t>(size, c->off[ch + 1] - s);
+            tiles.push_back(t);
         }
     }
-    c->tile_off_h[c->C] = (int)c->tiles_h.size();
-    c->n_tiles = (int)c->tiles_h.size();
+    off[c->C] = (int)tiles.size();
 }
 
 // Split-K work of the tensor-core adjoint: the (channel, output block)
@@ -490,7 +491,7 @@ mem_status after_launch(mem_ctx* c, const char* what) {
 // Buffers needed by the current precision.
 mem_status ensure_buffers(mem_ctx* c) {
     const size_t NN = (size_t)c->N * c->N;
-    TRY(dalloc(c, &c->chi_part, (size_t)4 * std::max(c->n_tiles, 1)));
+    TRY(dalloc(c, &c->chi_part, (size_t)4 * std::max(std::max(c->n_tiles, c->n_tiles_tc), 1)));
     TRY(dalloc(c, &c->ent_part, (size_t)c->n_images * prep_blocks(c->N)));
     TRY(dalloc(c, &c->scal, (size_t)3 + 3 * c->n_images));
     TRY(dalloc(c, &c->img_tmp, (size_t)scalars_tmp_doubles(c->n_images)));
@@ -502,6 +503,7 @@ mem_status ensure_buffers(mem_ctx* c) {
         TRY(dalloc(c, &c->bf32, (size_t)c->C * NN));
     } else {
         TRY(dalloc(c, &c->planes, (size_t)2 * c->C * NN));
+        TRY(dalloc(c, &c->cmean, (size_t)c->C * c->N));
         const int BLK = tca_blk(c->N);
         TRY(dalloc(c, &c->partial, std::max<size_t>(c->units_h.size(), 1) * BLK * BLK));
     }
@@ -527,26 +529,34 @@ void* bbuf(mem_ctx* c) {
 // prep + forward for one image source.  mode: FwdMode.
 mem_status run_forward(mem_ctx* c, const ImgSrc& src, int mode, bool entropy, void* yout) {
     DevData d = c->dd();
+    const bool tc = c->prec == MEM_PREC_BF16X3;
+    if (tc) {
+        KTimer t(c, "colmean");
+        launch_colmean(d, src, c->cmean, c->st);
+        c->launches++;
+    }
     {
         KTimer t(c, "prep");
-        launch_prep(d, src, bformat(c->prec), bbuf(c), entropy ? c->ent_part : nullptr, c->st);
+        launch_prep(d, src, bformat(c->prec), bbuf(c), entropy ? c->ent_part : nullptr, tc ? c->cmean : nullptr,
+                    c->st);
     }
     c->launches++;
     TRY(after_launch(c, "prep kernel"));
-    if (c->prec == MEM_PREC_BF16X3) {
+    if (tc) {
         KTimer t(c, "fwd_tc");
-        launch_fwd_tc(d, c->tiles, c->n_tiles, c->planes, mode, (float2*)yout, c->chi_part,
+        launch_fwd_tc(d, c->tiles_tc, c->n_tiles_tc, c->planes, c->cmean, mode, (float2*)yout, c->chi_part,
                       c->num_sms, c->spin, c->dstatus, c->st);
     } else {
         KTimer t(c, c->prec == MEM_PREC_FP64_DIRECT ? "fwd_direct_f64" : "fwd_direct_f32");
         launch_fwd_direct(d, c->prec == MEM_PREC_FP64_DIRECT, c->tiles, c->n_tiles, bbuf(c), mode, yout,
                           c->chi_part, c->st);
     }
-    if (c->n_tiles > 0) c->launches++;
+    if ((tc ? c->n_tiles_tc : c->n_tiles) > 0) c->launches++;
     TRY(after_launch(c, "forward kernel"));
     if (mode != FWD_VIS) {
         KTimer t(c, "scalars");
-        launch_scalars(d, c->tile_off, c->chi_part, c->ent_part, entropy ? 1 : 0, c->scal, c->img_tmp, c->st);
+        launch_scalars(d, tc ? c->tile_off_tc : c->tile_off, c->chi_part, c->ent_part, entropy ? 1 : 0,
+                       c->scal, c->img_tmp, c->st);
         c->launches += 2;
         TRY(after_launch(c, "scalar reduction"));
     }
@@ -780,10 +790,15 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
     launch_phase_prep(Z, c->u, c->v, c->dx, c->dy, c->pa, c->pb, c->st);
     c->launches++;
 
-    build_tiles(c);
+    build_tiles(c, 128, c->tiles_h, c->tile_off_h);
+    build_tiles(c, TC_TILE, c->tiles_tc_h, c->tile_off_tc_h);
+    c->n_tiles = (int)c->tiles_h.size();
+    c->n_tiles_tc = (int)c->tiles_tc_h.size();
     build_units(c);
     if ((s = dalloc(c, &c->tiles, std::max<size_t>(c->tiles_h.size(), 1))) ||
         (s = dalloc(c, &c->tile_off, c->tile_off_h.size())) ||
+        (s = dalloc(c, &c->tiles_tc, std::max<size_t>(c->tiles_tc_h.size(), 1))) ||
+        (s = dalloc(c, &c->tile_off_tc, c->tile_off_tc_h.size())) ||
         (s = dalloc(c, &c->units, std::max<size_t>(c->units_h.size(), 1))) ||
         (s = dalloc(c, &c->cta_off, c->cta_off_h.size())) || (s = dalloc(c, &c->cb_off, c->cb_off_h.size()))) {
         g_last_error = c->err;
@@ -791,6 +806,9 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
     }
     e = cpy(c->tiles, c->tiles_h.data(), c->tiles_h.size() * sizeof(VisTile));
     if (e == cudaSuccess) e = cpy(c->tile_off, c->tile_off_h.data(), c->tile_off_h.size() * sizeof(int));
+    if (e == cudaSuccess) e = cpy(c->tiles_tc, c->tiles_tc_h.data(), c->tiles_tc_h.size() * sizeof(VisTile));
+    if (e == cudaSuccess)
+        e = cpy(c->tile_off_tc, c->tile_off_tc_h.data(), c->tile_off_tc_h.size() * sizeof(int));
     if (e == cudaSuccess) e = cpy(c->units, c->units_h.data(), c->units_h.size() * sizeof(AdjUnit));
     if (e == cudaSuccess) e = cpy(c->cta_off, c->cta_off_h.data(), c->cta_off_h.size() * sizeof(int));
     if (e == cudaSuccess) e = cpy(c->cb_off, c->cb_off_h.data(), c->cb_off_h.size() * sizeof(int));

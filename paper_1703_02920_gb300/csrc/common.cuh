@@ -95,16 +95,20 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 
 // Bounded wait: gives up after `limit` polls or when another role of the CTA
 // has already given up (*abort != 0); on give-up sets the device status and
-// the CTA's abort flag.  Returns true when the phase completed.
+// the CTA's abort flag.  Returns true when the phase completed.  sleep_ns > 0
+// backs off between polls (for long waits, so that waiting warps leave the
+// issue slots to working ones); the poll bound is then limit / 16.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit,
-                                          volatile int* abort, int* status) {
+                                          volatile int* abort, int* status, unsigned sleep_ns = 0) {
     uint64_t it = 0;
+    const uint64_t lim = sleep_ns ? (limit >> 4 ? limit >> 4 : 1) : limit;
     while (!mbar_try_wait(bar, parity)) {
-        if (++it >= limit || *abort) {
+        if (++it >= lim || *abort) {
             *abort = 1;
             atomicOr(status, DEV_TIMEOUT);
             return false;
         }
+        if (sleep_ns) __nanosleep(sleep_ns);
     }
     return true;
 }

@@ -9,7 +9,8 @@ namespace msk {
 // Device status word bits (the host maps them to mem_status).
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADARG = 2 };
 
-// 128 consecutive visibilities of one channel (the forward kernels' unit).
+// Consecutive visibilities of one channel (the forward kernels' unit: 128 for
+// the direct forms, TC_TILE for the tensor-core form).
 struct VisTile {
     int32_t chan;
     int32_t count;
@@ -63,9 +64,11 @@ enum BFormat { BF_F32 = 0, BF_F64 = 1, BF_BF16X3 = 2 };
 //   image read from the y buffer.
 enum FwdMode { FWD_VIS = 0, FWD_RESID = 1, FWD_CHI = 2, FWD_CURV = 3, FWD_DCHI = 4 };
 
-// Forward tensor-core tiling: m-block width and n per pipeline stage.
+// Forward tensor-core tiling: 64 visibilities per tile, image column block
+// width BN and image rows per pipeline stage.
 constexpr int TC_BK = 32;
-inline int tc_bn(int N) { return N < 128 ? N : 128; }
+constexpr int TC_TILE = 64;
+__host__ __device__ inline int tc_bn(int N) { return N < 256 ? N : 256; }
 // Adjoint tensor-core tiling: output block side and visibilities per stage.
 constexpr int TCA_BK = 16;
 inline int tca_blk(int N) { return N < 256 ? N : 256; }
@@ -78,9 +81,12 @@ void launch_phase_prep(int64_t Z, const double* u, const double* v, double dx, d
                        uint64_t* pa, uint64_t* pb, cudaStream_t st);
 
 // B_c = A_c * img(c) for every channel in the requested format; entropy
-// partials S_i per (image, block) when ent_part != nullptr.
+// partials S_i per (image, block) when ent_part != nullptr.  With cmean
+// (BF16X3 only) the planes hold B - c_m, c_m the column mean.
 void launch_prep(const DevData& d, const ImgSrc& src, int fmt, void* bout, double* ent_part,
-                 cudaStream_t st);
+                 const float* cmean, cudaStream_t st);
+// Column means of B_c per channel into cmean[C][N].
+void launch_colmean(const DevData& d, const ImgSrc& src, float* cmean, cudaStream_t st);
 int prep_blocks(int N);
 
 void launch_fwd_direct(const DevData& d, int fp64, const VisTile* tiles, int n_tiles, const void* B,
@@ -93,8 +99,8 @@ int adj_direct_splits(const DevData& d, int num_sms);
 // Tensor-core forms.
 int fwd_tc_smem_bytes(int N);
 void launch_fwd_tc(const DevData& d, const VisTile* tiles, int n_tiles, const void* planes,
-                   int mode, float2* yout, double* chi_part, int grid, uint64_t spin, int* status,
-                   cudaStream_t st);
+                   const float* cmean, int mode, float2* yout, double* chi_part, int grid,
+                   uint64_t spin, int* status, cudaStream_t st);
 int adj_tc_smem_bytes(int N);
 // units sorted by CTA: CTA b runs units [cta_unit_off[b], cta_unit_off[b+1]).
 void launch_adj_tc(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,

@@ -1,0 +1,354 @@
+// Tensor-core forward operator (Eq. 1 on the pixel grid) with the fused
+// per-visibility reduction, residual, weight and chi^2 partials.
+//
+//   T = Ey B^T  (tcgen05.mma kind::f16, 3-term split BF16, FP32 accumulation)
+//   V_k = sum_m Ex[k,m] T[k,m]
+//
+// The image operand is centred column by column, B'[n][m] = B[n][m] - c_m
+// (c_m the column mean), and T = Ey B'^T + c_m S_k with the closed form
+//   S_k = sum_n Ey[k,n] = exp(i pi b_k) sin(pi N b_k) / sin(pi b_k),  b_k = frac(v_k dy).
+// For low spatial frequencies the uncentred partial sums grow monotonically
+// and the tensor core's FP32 accumulation (which rounds towards zero) then
+// shrinks T systematically; the centred sums wander around zero instead.
+//
+// A tile is 64 visibilities.  Its A operand has 128 rows: row 2j holds
+// Re Ey[j,:], row 2j+1 holds Im Ey[j,:], so one M=128 MMA produces both the
+// real and the imaginary part of T for 64 visibilities, and one N <= 256
+// column block covers an N <= 256 image without regenerating Ey.  Two TMEM
+// accumulators (2 x BN columns) let the epilogue of one tile overlap the MMAs
+// of the next.
+//
+// Roles (448 threads): warps 0-3 epilogue (TMEM lane = A row), warp 4 MMA
+// issuer + TMEM owner, warp 5 bulk copies of the image operand chunks,
+// warps 6-13 Ey producers.  Every mbarrier wait is bounded.
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace msk {
+
+namespace {
+
+constexpr int F2_STAGES = 4;
+constexpr int F2_THREADS = 448;
+constexpr int F2_APLANE = 128 * TC_BK * 2;  // bytes of one A plane (hi or lo), 8 KB
+constexpr int F2_ABYTES = 2 * F2_APLANE;
+
+__host__ __device__ inline int f2_stage_bytes(int BN) { return F2_ABYTES + 2 * BN * TC_BK * 2; }
+__host__ __device__ inline uint32_t f2_tmem_cols(int BN) {
+    uint32_t c = 32;
+    while ((int)c < 2 * BN) c <<= 1;
+    return c;
+}
+
+__device__ __forceinline__ cf2 cis_neg(uint64_t p) {
+    float s, c;
+    __sincosf(phase_to_angle_f32(p), &s, &c);
+    return {c, -s};
+}
+
+struct F2Shared {
+    uint64_t full[F2_STAGES];   // producer warps (8 arrivals)
+    uint64_t bfull[F2_STAGES];  // image operand bulk copy (transaction bytes)
+    uint64_t empty[F2_STAGES];  // MMA completion (tcgen05.commit)
+    uint64_t tfull[2];
+    uint64_t tempty[2];         // 4 epilogue warps
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__global__ void __launch_bounds__(F2_THREADS, 1)
+    k_fwd_tc(DevData d, const VisTile* __restrict__ tiles, int n_tiles,
+             const __nv_bfloat16* __restrict__ planes, const float* __restrict__ cmean, int mode,
+             float2* __restrict__ yout, double* __restrict__ chi_part, uint64_t spin, int* status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ F2Shared S;
+    const int N = d.N, c0 = N / 2;
+    const int BN = tc_bn(N);
+    const int n_mb = N / BN, nk = N / TC_BK;
+    const int stage_bytes = f2_stage_bytes(BN);
+    const uint32_t tcols = f2_tmem_cols(BN);
+    const int64_t NN = (int64_t)N * N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* abort = &S.abort;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < F2_STAGES; ++s) {
+            mbar_init(&S.full[s], 8);
+            mbar_init(&S.bfull[s], 1);
+            mbar_init(&S.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&S.tfull[b], 1);
+            mbar_init(&S.tempty[b], 4);
+        }
+        mbar_init(&S.drain, 1);
+        S.abort = 0;
+        mbar_fence_init();
+    }
+    if (warp == 4) {
+        tmem_alloc(&S.tmem_base, tcols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    if (warp == 4) {
+        // ---------------------------------------------------------------- MMA
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(128, BN, 0, 0);
+            const uint32_t sbase = smem_u32(smem);
+            const uint32_t lboB = (uint32_t)(BN / 8) * 128;
+            uint32_t sc = 0, it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                for (int mb = 0; mb < n_mb && ok; ++mb, ++it) {
+                    const int b = it & 1;
+                    ok = mbar_wait(&S.tempty[b], ((it >> 1) & 1) ^ 1, spin, abort, status);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t dt = tmem + (uint32_t)(b * BN);
+                    for (int ks = 0; ks < nk; ++ks, ++sc) {
+                        const int s = sc % F2_STAGES;
+                        ok = mbar_wait(&S.full[s], (sc / F2_STAGES) & 1, spin, abort, status) &&
+                             mbar_wait(&S.bfull[s], (sc / F2_STAGES) & 1, spin, abort, status);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t A = sbase + s * stage_bytes;
+                        const uint32_t B = A + F2_ABYTES;
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                            const uint32_t ao = kk * 2 * 2048, bo = kk * 2 * lboB;
+                            const uint64_t a_h = smem_desc(A + ao, 2048, 128);
+                            const uint64_t a_l = smem_desc(A + F2_APLANE + ao, 2048, 128);
+                            const uint64_t b_h = smem_desc(B + bo, lboB, 128);
+                            const uint64_t b_l = smem_desc(B + BN * TC_BK * 2 + bo, lboB, 128);
+                            const uint32_t acc = (ks > 0 || kk > 0) ? 1u : 0u;
+                            umma_bf16(dt, a_h, b_h, idesc, acc);
+                            umma_bf16(dt, a_h, b_l, idesc, 1u);
+                            umma_bf16(dt, a_l, b_h, idesc, 1u);
+                        }
+                        umma_commit(&S.empty[s]);
+                    }
+                    if (ok) umma_commit(&S.tfull[b]);
+                }
+            }
+            // every issued MMA completes before TMEM is released (its operands
+            // were complete when it was issued)
+            umma_commit(&S.drain);
+            int dummy = 0;
+            mbar_wait(&S.drain, 0, 1ull << 32, (volatile int*)&dummy, status);
+        }
+        __syncwarp();
+    } else if (warp == 5) {
+        // --------------------------------------------- image operand copies
+        if (lane == 0) {
+            uint32_t sc = 0;
+            bool ok = true;
+            const uint32_t chunk_bytes = 2u * BN * TC_BK * 2;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                const int chan = tiles[t].chan;
+                const unsigned char* cbase = (const unsigned char*)(planes + (int64_t)chan * 2 * NN);
+                for (int mb = 0; mb < n_mb && ok; ++mb) {
+                    for (int ks = 0; ks < nk; ++ks, ++sc) {
+                        const int s = sc % F2_STAGES;
+                        ok = mbar_wait(&S.empty[s], ((sc / F2_STAGES) & 1) ^ 1, spin, abort, status);
+                        if (!ok) break;
+                        mbar_arrive_expect_tx(&S.bfull[s], chunk_bytes);
+                        bulk_g2s(smem + s * stage_bytes + F2_ABYTES,
+                                 cbase + (int64_t)(mb * nk + ks) * chunk_bytes, chunk_bytes, &S.bfull[s]);
+                    }
+                }
+            }
+            if (!ok) {
+                // copies already issued land on their own; wait for them before
+                // the CTA's shared memory is released
+                int dummy = 0;
+                for (uint32_t q = (sc > F2_STAGES ? sc - F2_STAGES : 0); q < sc; ++q)
+                    mbar_wait(&S.bfull[q % F2_STAGES], (q / F2_STAGES) & 1, 1ull << 32,
+                              (volatile int*)&dummy, status);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 6) {
+        // ----------------------------------- Ey producers (256 threads)
+        // thread -> (visibility j = ptid & 63, k-group g = ptid >> 6): 8 image
+        // rows n of one visibility per stage, written as rows 2j (Re), 2j+1 (Im)
+        const int ptid = threadIdx.x - 192;
+        const int jv = ptid & 63, g = ptid >> 6;
+        const int r0 = 2 * jv;
+        const int off = (g * 16 + (r0 >> 3)) * 128 + (r0 & 7) * 16;  // row 2j; row 2j+1 at +16
+        uint32_t sc = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            const VisTile tl = tiles[t];
+            const bool valid = jv < tl.count;
+            const uint64_t pb = valid ? d.pb[tl.start + jv] : 0;
+            cf2 step[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) step[q] = cis_neg(phase_mul(q, pb));
+            for (int mb = 0; mb < n_mb && ok; ++mb) {
+                for (int ks = 0; ks < nk; ++ks, ++sc) {
+                    const int s = sc % F2_STAGES;
+                    ok = __all_sync(0xffffffffu, mbar_wait(&S.empty[s], ((sc / F2_STAGES) & 1) ^ 1, spin,
+                                                           abort, status, 64));
+                    if (!ok) break;
+                    unsigned char* A = smem + s * stage_bytes;
+                    uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
+                    if (valid) {
+                        const int n0 = ks * TC_BK + g * 8;
+                        const cf2 base = cis_neg(phase_mul(n0 - c0, pb));
+                        cf2 z[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) z[q] = cmul(base, step[q]);
+                        split_bf16x2(z[0].x, z[1].x, rh.x, rl.x);
+                        split_bf16x2(z[2].x, z[3].x, rh.y, rl.y);
+                        split_bf16x2(z[4].x, z[5].x, rh.z, rl.z);
+                        split_bf16x2(z[6].x, z[7].x, rh.w, rl.w);
+                        split_bf16x2(z[0].y, z[1].y, ih.x, il.x);
+                        split_bf16x2(z[2].y, z[3].y, ih.y, il.y);
+                        split_bf16x2(z[4].y, z[5].y, ih.z, il.z);
+                        split_bf16x2(z[6].y, z[7].y, ih.w, il.w);
+                    }
+                    *(uint4*)(A + off) = rh;
+                    *(uint4*)(A + off + 16) = ih;
+                    *(uint4*)(A + F2_APLANE + off) = rl;
+                    *(uint4*)(A + F2_APLANE + off + 16) = il;
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S.full[s]);
+                }
+            }
+        }
+    } else {
+        // -------------------------------- epilogue (warps 0-3, 128 threads)
+        // lane r = A row: visibility j = r / 2, component r & 1 (0: Re T, 1: Im T).
+        // Every lane accumulates (sum ReEx T, sum ImEx T) over its row; the
+        // even/odd pair combines with one shuffle:
+        //   Re V = sum ReEx ReT - ImEx ImT,  Im V = sum ReEx ImT + ImEx ReT.
+        const int row = threadIdx.x;
+        const int jv = row >> 1, comp = row & 1;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            const VisTile tl = tiles[t];
+            const bool valid = jv < tl.count;
+            const int64_t j = tl.start + (valid ? jv : 0);
+            const uint64_t pa = d.pa[j];
+            cf2 step[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) step[q] = cis_neg(phase_mul(q, pa));
+            // this lane's component of S_j = sum_n Ey[j,n] (accurate sincospi of
+            // the exact half-turn and N/2-multiple phases)
+            float scomp;
+            {
+                const uint64_t pb = d.pb[j];
+                const float th = (float)(int64_t)((int64_t)pb >> 1) * 5.421010862427522e-20f;  // b/2, turns
+                const float tn = (float)(int64_t)phase_mul(N / 2, pb) * 5.421010862427522e-20f;  // N b/2
+                float sh, ch;
+                sincospif(2.0f * th, &sh, &ch);          // sin(pi b), cos(pi b)
+                const float snb = sinpif(2.0f * tn);      // sin(pi N b)
+                const float D = (sh != 0.f) ? snb / sh : (float)N;
+                scomp = comp ? sh * D : ch * D;
+            }
+            const float* cm = cmean + (int64_t)tl.chan * N;
+            float s0 = 0.f, s1 = 0.f, c0s = 0.f, c1s = 0.f;  // compensated sums
+            for (int mb = 0; mb < n_mb; ++mb, ++it) {
+                const int b = it & 1;
+                ok = __all_sync(0xffffffffu,
+                                mbar_wait(&S.tfull[b], (it >> 1) & 1, spin, abort, status, 256));
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * BN);
+                for (int q = 0; q < BN / 16; ++q) {
+                    uint32_t tv[16];
+                    tmem_ld16(lane_base + q * 16, tv);
+                    tmem_ld_wait();
+                    const int m0 = mb * BN + q * 16;
+                    const cf2 base = cis_neg(phase_mul(m0 - c0, pa));
+                    float cq[16];
+#pragma unroll
+                    for (int k = 0; k < 16; k += 4) {
+                        const float4 t4 = __ldg((const float4*)(cm + m0 + k));
+                        cq[k] = t4.x;
+                        cq[k + 1] = t4.y;
+                        cq[k + 2] = t4.z;
+                        cq[k + 3] = t4.w;
+                    }
+                    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const cf2 ex = cmul(base, step[k]);
+                        const float tk = fmaf(cq[k], scomp, __uint_as_float(tv[k]));
+                        a0 = fmaf(ex.x, tk, a0);
+                        a1 = fmaf(ex.y, tk, a1);
+                    }
+                    two_sum_acc(s0, c0s, a0);
+                    two_sum_acc(s1, c1s, a1);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.tempty[b]);
+            }
+            if (!ok) break;
+            // even lane: (sum ReEx ReT, sum ImEx ReT); odd lane: (sum ReEx ImT, sum ImEx ImT)
+            const double p0 = (double)s0 + (double)c0s, p1 = (double)s1 + (double)c1s;
+            const double q0 = __shfl_xor_sync(0xffffffffu, p0, 1);
+            const double q1 = __shfl_xor_sync(0xffffffffu, p1, 1);
+            double chi = 0.0;
+            if (valid && comp == 0) {
+                const double Vre = p0 - q1;  // ReEx ReT - ImEx ImT
+                const double Vim = q0 + p1;  // ReEx ImT + ImEx ReT
+                if (mode == FWD_VIS) {
+                    yout[j] = make_float2((float)Vre, (float)Vim);
+                } else if (mode == FWD_DCHI) {
+                    const float2 yv = yout[j];
+                    chi = (double)yv.x * Vre + (double)yv.y * Vim + 0.5 * d.w[j] * (Vre * Vre + Vim * Vim);
+                } else {
+                    double rr = Vre, ri = Vim;
+                    if (mode != FWD_CURV) {
+                        rr -= d.vo[j].x;
+                        ri -= d.vo[j].y;
+                    }
+                    const double w = d.w[j];
+                    chi = 0.5 * w * (rr * rr + ri * ri);
+                    if (mode == FWD_RESID) yout[j] = make_float2((float)(w * rr), (float)(w * ri));
+                }
+            }
+            if (mode != FWD_VIS) {
+                // one partial per warp (16 visibilities), summed later in a fixed order
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) chi += __shfl_down_sync(0xffffffffu, chi, o);
+                if (lane == 0) chi_part[(int64_t)t * 4 + warp] = chi;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        tc_fence_after();
+        tmem_dealloc(tmem, tcols);
+    }
+}
+
+}  // namespace
+
+int fwd_tc_smem_bytes(int N) { return F2_STAGES * f2_stage_bytes(tc_bn(N)) + 1024; }
+
+void launch_fwd_tc(const DevData& d, const VisTile* tiles, int n_tiles, const void* planes,
+                   const float* cmean, int mode, float2* yout, double* chi_part, int grid,
+                   uint64_t spin, int* status, cudaStream_t st) {
+    if (n_tiles <= 0) return;
+    const int smem = fwd_tc_smem_bytes(d.N);
+    cudaFuncSetAttribute(k_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (grid > n_tiles) grid = n_tiles;
+    k_fwd_tc<<<grid, F2_THREADS, smem, st>>>(d, tiles, n_tiles, (const __nv_bfloat16*)planes, cmean, mode,
+                                             yout, chi_part, spin, status);
+}
+
+}  // namespace msk

@@ -89,8 +89,41 @@ __device__ __forceinline__ int64_t tc_plane_index(int n, int m, int N, int BN) {
     return chunk * chunk_elems + off;  // in bf16 elements; lo at + BN*BK
 }
 
+// Column means c_m = (1/N) sum_n B[n][m] per channel (the operand of the
+// tensor-core forward is centred column by column, see k_fwd_tc).  Block:
+// 32 columns x 8 row groups, fixed summation order.
+__global__ void __launch_bounds__(256) k_colmean(DevData d, ImgSrc src, float* __restrict__ cmean) {
+    __shared__ double sh[8][33];
+    const int N = d.N;
+    const int64_t NN = (int64_t)N * N;
+    const int c = blockIdx.y;
+    const int i = image_of(d, c);
+    const int m = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int rg = threadIdx.x >> 5;
+    double acc = 0.0;
+    if (m < N) {
+        for (int n = rg; n < N; n += 8) {
+            const int64_t p = (int64_t)n * N + m;
+            double x = img_value(src, i, p, NN);
+            if (src.diff) x -= src.f64[(int64_t)i * NN + p];
+            acc += (double)d.beam[(int64_t)c * NN + p] * x;
+        }
+    }
+    sh[rg][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (rg == 0 && m < N) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += sh[k][threadIdx.x];
+        cmean[(int64_t)c * N + m] = (float)(t / N);
+    }
+}
+
+void launch_colmean(const DevData& d, const ImgSrc& src, float* cmean, cudaStream_t st) {
+    k_colmean<<<dim3((d.N + 31) / 32, d.C), 256, 0, st>>>(d, src, cmean);
+}
+
 __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, void* bout,
-                                              double* ent_part) {
+                                              double* ent_part, const float* __restrict__ cmean) {
     __shared__ double sh[8];
     const int N = d.N;
     const int64_t NN = (int64_t)N * N;
@@ -118,8 +151,8 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
             ((double*)bout)[(int64_t)c * NN + p] = b;
         } else {
             int n = (int)(p / N), m = (int)(p % N);
-            int BN = N < 128 ? N : 128;
-            float bf = (float)b;
+            int BN = tc_bn(N);
+            float bf = (float)(b - (cmean ? (double)cmean[(int64_t)c * N + m] : 0.0));
             __nv_bfloat16 hi = __float2bfloat16_rn(bf);
             __nv_bfloat16 lo = __float2bfloat16_rn(bf - __bfloat162float(hi));
             __nv_bfloat16* base = (__nv_bfloat16*)bout + (int64_t)c * 2 * NN;
@@ -138,9 +171,9 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
 int prep_blocks(int N) { return (int)(((int64_t)N * N + 255) / 256); }
 
 void launch_prep(const DevData& d, const ImgSrc& src, int fmt, void* bout, double* ent_part,
-                 cudaStream_t st) {
+                 const float* cmean, cudaStream_t st) {
     dim3 grid(prep_blocks(d.N), d.C);
-    k_prep<<<grid, 256, 0, st>>>(d, src, fmt, bout, ent_part);
+    k_prep<<<grid, 256, 0, st>>>(d, src, fmt, bout, ent_part, cmean);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,4 +1,5 @@
-// Tensor-core (tcgen05) forms of the measurement operator and its adjoint.
+// Tensor-core (tcgen05) adjoint of the measurement operator (the forward
+// operator is in kernels_fwd.cu).
 //
 // On the regular pixel grid the phase of Eq. (1) separates,
 //   exp(-2 pi i (u x_m + v y_n)) = Ex[k,m] Ey[k,n],
@@ -29,293 +30,6 @@ __device__ __forceinline__ cf2 cis_neg(uint64_t p) {
     float s, c;
     __sincosf(phase_to_angle_f32(p), &s, &c);
     return {c, -s};
-}
-
-// ===========================================================================
-// Forward: T = Ey B^T on tensor cores, fused V_k = sum_m Ex T, residual, chi^2.
-// CTA roles: warps 0-3 epilogue (TMEM lanes 0-127 = the tile's 128
-// visibilities), warp 4 MMA issuer + TMEM owner, warp 5 bulk copies of the
-// image operand, warps 6-13 phase-table producers.
-// ===========================================================================
-constexpr int FWD_STAGES = 4;
-constexpr int FWD_THREADS = 448;
-constexpr int FWD_A_PLANE = 128 * TC_BK * 2;       // bytes per A plane (8 KB)
-constexpr int FWD_A_BYTES = 4 * FWD_A_PLANE;        // Re hi, Re lo, Im hi, Im lo
-
-__host__ __device__ inline int fwd_stage_bytes(int BN) { return FWD_A_BYTES + 2 * BN * TC_BK * 2; }
-
-int fwd_tc_smem_bytes(int N) { return FWD_STAGES * fwd_stage_bytes(tc_bn(N)) + 1024; }
-
-struct FwdShared {
-    uint64_t full[FWD_STAGES];   // producer warps (8 arrivals)
-    uint64_t bfull[FWD_STAGES];  // image operand bulk copy (transaction count)
-    uint64_t empty[FWD_STAGES];
-    uint64_t tfull[2];
-    uint64_t tempty[2];
-    uint64_t drain;
-    uint32_t tmem_base;
-    int abort;
-};
-
-__global__ void __launch_bounds__(FWD_THREADS, 1)
-    k_fwd_tc(DevData d, const VisTile* __restrict__ tiles, int n_tiles,
-             const __nv_bfloat16* __restrict__ planes, int mode, float2* __restrict__ yout,
-             double* __restrict__ chi_part, uint64_t spin, int* status) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ FwdShared S;
-    const int N = d.N, c0 = N / 2;
-    const int BN = N < 128 ? N : 128;
-    const int n_mb = N / BN, nk = N / TC_BK;
-    const int stage_bytes = fwd_stage_bytes(BN);
-    const int64_t NN = (int64_t)N * N;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    volatile int* abort = &S.abort;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < FWD_STAGES; ++s) {
-            mbar_init(&S.full[s], 8);
-            mbar_init(&S.bfull[s], 1);
-            mbar_init(&S.empty[s], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&S.tfull[b], 1);
-            mbar_init(&S.tempty[b], 4);
-        }
-        mbar_init(&S.drain, 1);
-        S.abort = 0;
-        mbar_fence_init();
-    }
-    if (warp == 4) {
-        tmem_alloc(&S.tmem_base, 512);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = S.tmem_base;
-
-    if (warp == 4) {
-        // ------------------------------------------------------------ MMA
-        if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(128, BN, 0, 0);
-            const uint32_t sbase = smem_u32(smem);
-            uint32_t sc = 0, it = 0;
-            bool ok = true;
-            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                for (int mb = 0; mb < n_mb && ok; ++mb, ++it) {
-                    const int b = it & 1;
-                    ok = mbar_wait(&S.tempty[b], ((it >> 1) & 1) ^ 1, spin, abort, status);
-                    if (!ok) break;
-                    tc_fence_after();
-                    const uint32_t d_re = tmem + (uint32_t)(b * 256);
-                    const uint32_t d_im = d_re + 128;
-                    for (int ks = 0; ks < nk; ++ks, ++sc) {
-                        const int s = sc % FWD_STAGES;
-                        ok = mbar_wait(&S.full[s], (sc / FWD_STAGES) & 1, spin, abort, status) &&
-                             mbar_wait(&S.bfull[s], (sc / FWD_STAGES) & 1, spin, abort, status);
-                        if (!ok) break;
-                        tc_fence_after();
-                        const uint32_t A = sbase + s * stage_bytes;
-                        const uint32_t B = A + FWD_A_BYTES;
-#pragma unroll
-                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                            const uint32_t ao = kk * 2 * 2048, bo = kk * 2 * 16 * BN;
-                            uint64_t are_h = smem_desc(A + 0 * FWD_A_PLANE + ao, 2048, 128);
-                            uint64_t are_l = smem_desc(A + 1 * FWD_A_PLANE + ao, 2048, 128);
-                            uint64_t aim_h = smem_desc(A + 2 * FWD_A_PLANE + ao, 2048, 128);
-                            uint64_t aim_l = smem_desc(A + 3 * FWD_A_PLANE + ao, 2048, 128);
-                            uint64_t b_h = smem_desc(B + bo, 16 * BN, 128);
-                            uint64_t b_l = smem_desc(B + BN * TC_BK * 2 + bo, 16 * BN, 128);
-                            uint32_t acc = (ks > 0 || kk > 0) ? 1u : 0u;
-                            umma_bf16(d_re, are_h, b_h, idesc, acc);
-                            umma_bf16(d_re, are_h, b_l, idesc, 1u);
-                            umma_bf16(d_re, are_l, b_h, idesc, 1u);
-                            umma_bf16(d_im, aim_h, b_h, idesc, acc);
-                            umma_bf16(d_im, aim_h, b_l, idesc, 1u);
-                            umma_bf16(d_im, aim_l, b_h, idesc, 1u);
-                        }
-                        umma_commit(&S.empty[s]);
-                    }
-                    if (ok) umma_commit(&S.tfull[b]);
-                }
-            }
-            // all issued MMAs complete before TMEM is released (they always
-            // finish: their operands were complete when they were issued)
-            umma_commit(&S.drain);
-            int dummy = 0;
-            mbar_wait(&S.drain, 0, 1ull << 32, (volatile int*)&dummy, status);
-        }
-        __syncwarp();
-    } else if (warp == 5) {
-        // ------------------------------------------------ image operand copies
-        if (lane == 0) {
-            uint32_t sc = 0;
-            bool ok = true;
-            const uint32_t chunk_bytes = 2u * BN * TC_BK * 2;
-            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                const int chan = tiles[t].chan;
-                const unsigned char* cbase = (const unsigned char*)(planes + (int64_t)chan * 2 * NN);
-                for (int mb = 0; mb < n_mb && ok; ++mb) {
-                    for (int ks = 0; ks < nk; ++ks, ++sc) {
-                        const int s = sc % FWD_STAGES;
-                        ok = mbar_wait(&S.empty[s], ((sc / FWD_STAGES) & 1) ^ 1, spin, abort, status);
-                        if (!ok) break;
-                        mbar_arrive_expect_tx(&S.bfull[s], chunk_bytes);
-                        bulk_g2s(smem + s * stage_bytes + FWD_A_BYTES,
-                                 cbase + (int64_t)(mb * nk + ks) * chunk_bytes, chunk_bytes, &S.bfull[s]);
-                    }
-                }
-            }
-            if (!ok) {
-                // copies already issued land on their own; wait for them before
-                // the CTA's shared memory is released
-                int dummy = 0;
-                for (uint32_t q = (sc > FWD_STAGES ? sc - FWD_STAGES : 0); q < sc; ++q)
-                    mbar_wait(&S.bfull[q % FWD_STAGES], (q / FWD_STAGES) & 1, 1ull << 32,
-                              (volatile int*)&dummy, status);
-            }
-        }
-        __syncwarp();
-    } else if (warp >= 6) {
-        // ------------------------------------------- Ey tile producers (256 thr)
-        const int ptid = threadIdx.x - 192;
-        const int row = ptid & 127;
-        uint32_t sc = 0;
-        bool ok = true;
-        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-            const VisTile tl = tiles[t];
-            const bool valid = row < tl.count;
-            const uint64_t pb = valid ? d.pb[tl.start + row] : 0;
-            cf2 step[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) step[q] = cis_neg(phase_mul(q, pb));
-            for (int mb = 0; mb < n_mb && ok; ++mb) {
-                for (int ks = 0; ks < nk; ++ks, ++sc) {
-                    const int s = sc % FWD_STAGES;
-                    ok = __all_sync(0xffffffffu,
-                                    mbar_wait(&S.empty[s], ((sc / FWD_STAGES) & 1) ^ 1, spin, abort, status));
-                    if (!ok) break;
-                    unsigned char* A = smem + s * stage_bytes;
-#pragma unroll
-                    for (int gi = 0; gi < 2; ++gi) {
-                        const int g = (ptid >> 7) + 2 * gi;  // k-group (8 image rows n)
-                        uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
-                        if (valid) {
-                            const int n0 = ks * TC_BK + g * 8;
-                            const cf2 base = cis_neg(phase_mul(n0 - c0, pb));
-                            cf2 z[8];
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) z[q] = cmul(base, step[q]);
-                            split_bf16x2(z[0].x, z[1].x, rh.x, rl.x);
-                            split_bf16x2(z[2].x, z[3].x, rh.y, rl.y);
-                            split_bf16x2(z[4].x, z[5].x, rh.z, rl.z);
-                            split_bf16x2(z[6].x, z[7].x, rh.w, rl.w);
-                            split_bf16x2(z[0].y, z[1].y, ih.x, il.x);
-                            split_bf16x2(z[2].y, z[3].y, ih.y, il.y);
-                            split_bf16x2(z[4].y, z[5].y, ih.z, il.z);
-                            split_bf16x2(z[6].y, z[7].y, ih.w, il.w);
-                        }
-                        const int off = (g * 16 + (row >> 3)) * 128 + (row & 7) * 16;
-                        *(uint4*)(A + 0 * FWD_A_PLANE + off) = rh;
-                        *(uint4*)(A + 1 * FWD_A_PLANE + off) = rl;
-                        *(uint4*)(A + 2 * FWD_A_PLANE + off) = ih;
-                        *(uint4*)(A + 3 * FWD_A_PLANE + off) = il;
-                    }
-                    fence_async_smem();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&S.full[s]);
-                }
-            }
-        }
-    } else {
-        // ------------------------------------ epilogue (warps 0-3, 128 threads)
-        const int row = threadIdx.x;  // TMEM lane = visibility within tile
-        uint32_t it = 0;
-        bool ok = true;
-        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-            const VisTile tl = tiles[t];
-            const bool valid = row < tl.count;
-            const int64_t j = tl.start + (valid ? row : 0);
-            const uint64_t pa = d.pa[j];
-            cf2 step[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) step[q] = cis_neg(phase_mul(q, pa));
-            float vre = 0.f, vim = 0.f, cre = 0.f, cim = 0.f;  // compensated sums
-            for (int mb = 0; mb < n_mb; ++mb, ++it) {
-                const int b = it & 1;
-                ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull[b], (it >> 1) & 1, spin, abort, status));
-                if (!ok) break;
-                tc_fence_after();
-                const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 256);
-                for (int q = 0; q < BN / 16; ++q) {
-                    uint32_t tre[16], tim[16];
-                    tmem_ld16(lane_base + q * 16, tre);
-                    tmem_ld16(lane_base + 128 + q * 16, tim);
-                    tmem_ld_wait();
-                    const int m0 = mb * BN + q * 16;
-                    const cf2 base = cis_neg(phase_mul(m0 - c0, pa));
-                    float ar = 0.f, ai = 0.f;
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const cf2 ex = cmul(base, step[k]);
-                        const float tr = __uint_as_float(tre[k]), ti = __uint_as_float(tim[k]);
-                        ar = fmaf(ex.x, tr, fmaf(-ex.y, ti, ar));
-                        ai = fmaf(ex.x, ti, fmaf(ex.y, tr, ai));
-                    }
-                    two_sum_acc(vre, cre, ar);
-                    two_sum_acc(vim, cim, ai);
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S.tempty[b]);
-            }
-            if (!ok) break;
-            double chi = 0.0;
-            if (valid) {
-                const double Vre = (double)vre + (double)cre, Vim = (double)vim + (double)cim;
-                if (mode == FWD_VIS) {
-                    yout[j] = make_float2((float)Vre, (float)Vim);
-                } else if (mode == FWD_DCHI) {
-                    const float2 q = yout[j];
-                    chi = (double)q.x * Vre + (double)q.y * Vim + 0.5 * d.w[j] * (Vre * Vre + Vim * Vim);
-                } else {
-                    double rr = Vre, ri = Vim;
-                    if (mode != FWD_CURV) { rr -= d.vo[j].x; ri -= d.vo[j].y; }
-                    const double w = d.w[j];
-                    chi = 0.5 * w * (rr * rr + ri * ri);
-                    if (mode == FWD_RESID) yout[j] = make_float2((float)(w * rr), (float)(w * ri));
-                }
-            }
-            if (mode != FWD_VIS) {
-                // one partial per warp (32 visibilities), summed later in a fixed order
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) chi += __shfl_down_sync(0xffffffffu, chi, o);
-                if (lane == 0) chi_part[(int64_t)t * 4 + warp] = chi;
-            }
-        }
-    }
-
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 4) {
-        tc_fence_after();
-        tmem_dealloc(tmem, 512);
-    }
-}
-
-void launch_fwd_tc(const DevData& d, const VisTile* tiles, int n_tiles, const void* planes, int mode,
-                   float2* yout, double* chi_part, int grid, uint64_t spin, int* status,
-                   cudaStream_t st) {
-    if (n_tiles <= 0) return;
-    int smem = fwd_tc_smem_bytes(d.N);
-    static int configured = 0;
-    if (configured < smem) {
-        cudaFuncSetAttribute(k_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        configured = smem;
-    }
-    if (grid > n_tiles) grid = n_tiles;
-    k_fwd_tc<<<grid, FWD_THREADS, smem, st>>>(d, tiles, n_tiles, (const __nv_bfloat16*)planes, mode,
-                                              yout, chi_part, spin, status);
 }
 
 // ===========================================================================
@@ -451,28 +165,37 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             const AdjUnit un = units[u];
             const int blk_n0 = (un.block / nbx) * BLK, blk_m0 = (un.block % nbx) * BLK;
             const int nst = (int)((un.count + TCA_BK - 1) / TCA_BK);
+            // per-visibility inputs of the next stage are loaded one stage ahead
+            auto fetch = [&](int ks, uint64_t& fa, uint64_t& fb, float2& fy) {
+                const int64_t kv = (int64_t)ks * TCA_BK + jj;
+                fa = 0;
+                fb = 0;
+                fy = make_float2(0.f, 0.f);
+                if (ks < nst && kv < un.count) {
+                    if (FROM_UV) {
+                        fa = to_fixed_turns(d.u[un.start + kv] * d.dx);
+                        fb = to_fixed_turns(d.v[un.start + kv] * d.dy);
+                    } else {
+                        fa = d.pa[un.start + kv];
+                        fb = d.pb[un.start + kv];
+                    }
+                    fy = y[un.start + kv];
+                }
+            };
+            uint64_t na, nb;
+            float2 ny;
+            fetch(0, na, nb, ny);
             for (int ks = 0; ks < nst; ++ks, ++sc) {
                 const int s = sc % ADJ_STAGES;
-                ok = __all_sync(0xffffffffu,
-                                mbar_wait(&S.empty[s], ((sc / ADJ_STAGES) & 1) ^ 1, spin, abort, status));
+                const uint64_t pa = na, pb = nb;
+                const cf2 yv = {ny.x, ny.y};
+                const bool valid = (int64_t)ks * TCA_BK + jj < un.count;
+                fetch(ks + 1, na, nb, ny);
+                ok = __all_sync(0xffffffffu, mbar_wait(&S.empty[s], ((sc / ADJ_STAGES) & 1) ^ 1, spin,
+                                                       abort, status, 64));
                 if (!ok) break;
                 unsigned char* A = smem + s * stage_bytes;
                 unsigned char* B = A + 4 * a_plane;
-                const int64_t kv = (int64_t)ks * TCA_BK + jj;
-                const bool valid = kv < un.count;
-                uint64_t pa = 0, pb = 0;
-                cf2 yv = {0.f, 0.f};
-                if (valid) {
-                    if (FROM_UV) {
-                        pa = to_fixed_turns(d.u[un.start + kv] * d.dx);
-                        pb = to_fixed_turns(d.v[un.start + kv] * d.dy);
-                    } else {
-                        pa = d.pa[un.start + kv];
-                        pb = d.pb[un.start + kv];
-                    }
-                    const float2 t = y[un.start + kv];
-                    yv = {t.x, t.y};
-                }
                 // rotation steps exp(-i 2 pi q a), q = 0..7, by powers of one SFU value
                 cf2 sy[8], sx[8];
                 sy[0] = {1.f, 0.f};
@@ -551,7 +274,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
         bool ok = true;
         for (int u = u0; u < u1 && ok; ++u) {
             const int it = u - u0;
-            ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull, it & 1, spin, abort, status));
+            ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull, it & 1, spin, abort, status, 1024));
             if (!ok) break;
             tc_fence_after();
             float* out = partial + (int64_t)u * BLK * BLK;
