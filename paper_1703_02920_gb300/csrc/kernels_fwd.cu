@@ -239,9 +239,10 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             const bool valid = jv < tl.count;
             const int64_t j = tl.start + (valid ? jv : 0);
             const uint64_t pa = d.pa[j];
-            cf2 step[16];
+            cf2 step[8];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) step[q] = cis_neg(phase_mul(q, pa));
+            for (int q = 0; q < 8; ++q) step[q] = cis_neg(phase_mul(q, pa));
+            const cf2 step8 = cis_neg(phase_mul(8, pa));
             // this lane's component of S_j = sum_n Ey[j,n] (accurate sincospi of
             // the exact half-turn and N/2-multiple phases)
             float scomp;
@@ -264,31 +265,42 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * BN);
-                for (int q = 0; q < BN / 16; ++q) {
-                    uint32_t tv[16];
-                    tmem_ld16(lane_base + q * 16, tv);
-                    tmem_ld_wait();
+                // software pipeline over 16-column chunks: the TMEM load and the
+                // column means of chunk q+1 are in flight while chunk q is reduced
+                const int nq = BN / 16;
+                uint32_t tv[2][16];
+                float4 cq4[2][4];
+                auto load_chunk = [&](int q, int slot) {
+                    tmem_ld16(lane_base + q * 16, tv[slot]);
+                    const float4* src = (const float4*)(cm + mb * BN + q * 16);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) cq4[slot][k] = __ldg(src + k);
+                };
+                auto reduce_chunk = [&](int q, int slot) {
                     const int m0 = mb * BN + q * 16;
                     const cf2 base = cis_neg(phase_mul(m0 - c0, pa));
-                    float cq[16];
-#pragma unroll
-                    for (int k = 0; k < 16; k += 4) {
-                        const float4 t4 = __ldg((const float4*)(cm + m0 + k));
-                        cq[k] = t4.x;
-                        cq[k + 1] = t4.y;
-                        cq[k + 2] = t4.z;
-                        cq[k + 3] = t4.w;
-                    }
+                    const cf2 base8 = cmul(base, step8);
+                    const float* cq = (const float*)cq4[slot];
                     float a0 = 0.f, a1 = 0.f;
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        const cf2 ex = cmul(base, step[k]);
-                        const float tk = fmaf(cq[k], scomp, __uint_as_float(tv[k]));
+                        const cf2 ex = cmul(k < 8 ? base : base8, step[k & 7]);
+                        const float tk = fmaf(cq[k], scomp, __uint_as_float(tv[slot][k]));
                         a0 = fmaf(ex.x, tk, a0);
                         a1 = fmaf(ex.y, tk, a1);
                     }
                     two_sum_acc(s0, c0s, a0);
                     two_sum_acc(s1, c1s, a1);
+                };
+                load_chunk(0, 0);
+                tmem_ld_wait(tv[0]);
+                for (int q = 0; q < nq; q += 2) {
+                    load_chunk(q + 1, 1);  // nq is even
+                    reduce_chunk(q, 0);
+                    tmem_ld_wait(tv[1]);
+                    if (q + 2 < nq) load_chunk(q + 2, 0);
+                    reduce_chunk(q + 1, 1);
+                    if (q + 2 < nq) tmem_ld_wait(tv[0]);
                 }
                 tc_fence_before();
                 __syncwarp();
