@@ -167,7 +167,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 5])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32_direct", "fp64_direct"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "fp32_direct", "fp64_direct"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -258,7 +258,7 @@ def main():
     flops = 4.0 * units
     if name.startswith(("fwd", "adj")) and not name.endswith("reduce"):
         achieved = flops / (avg_ms * 1e-3) / 1e12
-        if name.endswith("tc"):
+        if name.endswith("tc"):  # both split forms run kind::f16 MMAs at the bf16 rate
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
@@ -283,8 +283,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16x3" if args.precision == "bf16x3" else
-                ("f32" if args.precision == "fp32_direct" else "f64"),
+                "vs_baseline": None,
+                "dtype": {"bf16x3": "bf16x3", "fp16x3": "f16x3", "fp32_direct": "f32", "fp64_direct": "f64"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.config], "precision": args.precision,
                            "image": f"{N}x{N}", "visibilities": Z, "parallelism": f"replicas x{world}",

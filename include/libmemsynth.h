@@ -72,9 +72,12 @@ typedef enum {
 typedef enum {
     MEM_PREC_FP64_DIRECT = 0,  /* one FP64 exponential per (visibility, pixel) pair */
     MEM_PREC_FP32_DIRECT = 1,  /* one FP32 (SFU) exponential per pair, FP64 partial sums */
-    MEM_PREC_BF16X3 = 2        /* separable phase tables generated on chip, tcgen05
+    MEM_PREC_BF16X3 = 2,       /* separable phase tables generated on chip, tcgen05
                                   tensor-core contractions in 3-term split BF16 with FP32
-                                  accumulation, FP64 cross-tile reductions */
+                                  accumulation, compensated cross-tile reductions */
+    MEM_PREC_FP16X3 = 3        /* as BF16X3 with a 3-term split FP16 (11-bit halves) and
+                                  power-of-two operand scaling: same speed, ~8x smaller
+                                  representation error */
 } mem_precision;
 
 typedef enum {

@@ -278,6 +278,10 @@ struct mem_ctx {
     double* bf64 = nullptr;
     uint16_t* planes = nullptr;
     float* cmean = nullptr;  // column means of the centred tensor-core operand
+    float *cmax = nullptr, *cscale = nullptr;   // FP16X3 operand scales per channel
+    double* col_psum = nullptr;                 // column-mean partial sums
+    float* col_pmax = nullptr;
+    float *yscale = nullptr, *ymax_part = nullptr;  // FP16X3 scale of the adjoint input
     float* partial = nullptr;
     int* dstatus = nullptr;
     float* stage = nullptr;  // host-call staging (image, gradient)
@@ -398,6 +402,7 @@ mem_status dalloc(mem_ctx* c, T** p, size_t count) {
     } while (0)
 
 bool tc_shape_ok(int N) { return N == 64 || N == 128 || (N >= 256 && N % 256 == 0); }
+bool is_tc(int prec) { return prec == MEM_PREC_BF16X3 || prec == MEM_PREC_FP16X3; }
 
 // Visibility tiles of `size` per channel, in channel order.
 void build_tiles(const mem_ctx* c, int size, std::vector<VisTile>& tiles, std::vector<int>& off) {
@@ -504,11 +509,17 @@ mem_status ensure_buffers(mem_ctx* c) {
     } else {
         TRY(dalloc(c, &c->planes, (size_t)2 * c->C * NN));
         TRY(dalloc(c, &c->cmean, (size_t)c->C * c->N));
+        TRY(dalloc(c, &c->cmax, (size_t)c->C * colmean_blocks(c->N)));
+        TRY(dalloc(c, &c->col_psum, (size_t)colmean_tmp_count(c->N, c->C)));
+        TRY(dalloc(c, &c->col_pmax, (size_t)colmean_tmp_count(c->N, c->C)));
+        TRY(dalloc(c, &c->cscale, (size_t)c->C));
+        TRY(dalloc(c, &c->yscale, (size_t)1));
+        TRY(dalloc(c, &c->ymax_part, (size_t)256));
         const int BLK = tca_blk(c->N);
         TRY(dalloc(c, &c->partial, std::max<size_t>(c->units_h.size(), 1) * BLK * BLK));
     }
     int ks = 1;
-    if (c->prec != MEM_PREC_BF16X3) ks = adj_direct_splits(c->dd(), c->num_sms);
+    if (!is_tc(c->prec)) ks = adj_direct_splits(c->dd(), c->num_sms);
     if (ks > c->gsum_ks) {
         // grow: the old block stays allocated until destroy (rare)
         c->gsum = nullptr;
@@ -519,7 +530,10 @@ mem_status ensure_buffers(mem_ctx* c) {
 }
 
 int bformat(int prec) {
-    return prec == MEM_PREC_FP64_DIRECT ? BF_F64 : prec == MEM_PREC_FP32_DIRECT ? BF_F32 : BF_BF16X3;
+    return prec == MEM_PREC_FP64_DIRECT   ? BF_F64
+           : prec == MEM_PREC_FP32_DIRECT ? BF_F32
+           : prec == MEM_PREC_FP16X3      ? BF_F16X3
+                                          : BF_BF16X3;
 }
 void* bbuf(mem_ctx* c) {
     return c->prec == MEM_PREC_FP64_DIRECT ? (void*)c->bf64
@@ -529,23 +543,24 @@ void* bbuf(mem_ctx* c) {
 // prep + forward for one image source.  mode: FwdMode.
 mem_status run_forward(mem_ctx* c, const ImgSrc& src, int mode, bool entropy, void* yout) {
     DevData d = c->dd();
-    const bool tc = c->prec == MEM_PREC_BF16X3;
+    const bool tc = is_tc(c->prec);
+    const int f16 = c->prec == MEM_PREC_FP16X3;
     if (tc) {
         KTimer t(c, "colmean");
-        launch_colmean(d, src, c->cmean, c->st);
-        c->launches++;
+        launch_colmean(d, src, c->cmean, c->cmax, c->col_psum, c->col_pmax, c->st);
+        c->launches += 2;
     }
     {
         KTimer t(c, "prep");
         launch_prep(d, src, bformat(c->prec), bbuf(c), entropy ? c->ent_part : nullptr, tc ? c->cmean : nullptr,
-                    c->st);
+                    c->cmax, c->cscale, c->st);
     }
     c->launches++;
     TRY(after_launch(c, "prep kernel"));
     if (tc) {
         KTimer t(c, "fwd_tc");
-        launch_fwd_tc(d, c->tiles_tc, c->n_tiles_tc, c->planes, c->cmean, mode, (float2*)yout, c->chi_part,
-                      c->num_sms, c->spin, c->dstatus, c->st);
+        launch_fwd_tc(d, f16, c->tiles_tc, c->n_tiles_tc, c->planes, c->cmean, c->cscale, mode, (float2*)yout,
+                      c->chi_part, c->num_sms, c->spin, c->dstatus, c->st);
     } else {
         KTimer t(c, c->prec == MEM_PREC_FP64_DIRECT ? "fwd_direct_f64" : "fwd_direct_f32");
         launch_fwd_direct(d, c->prec == MEM_PREC_FP64_DIRECT, c->tiles, c->n_tiles, bbuf(c), mode, yout,
@@ -566,15 +581,22 @@ mem_status run_forward(mem_ctx* c, const ImgSrc& src, int mode, bool entropy, vo
 // adjoint of y (already in y32 / y64) into gsum; returns ks used.
 mem_status run_adjoint(mem_ctx* c, int* ks_out) {
     DevData d = c->dd();
-    if (c->prec == MEM_PREC_BF16X3) {
+    if (is_tc(c->prec)) {
+        const int f16 = c->prec == MEM_PREC_FP16X3;
+        if (f16) {
+            KTimer t(c, "yscale");
+            launch_absmax_scale(2 * c->Z, (const float*)c->y32, c->ymax_part, c->yscale, c->st);
+            c->launches += 2;
+        }
         if (c->adj_ctas > 0) {
             KTimer t(c, "adj_tc");
-            launch_adj_tc(d, c->units, c->cta_off, c->adj_ctas, c->y32, c->partial, c->spin, c->dstatus, c->st);
+            launch_adj_tc(d, f16, c->units, c->cta_off, c->adj_ctas, c->y32, c->yscale, c->partial, c->spin,
+                          c->dstatus, c->st);
             c->launches++;
             TRY(after_launch(c, "adjoint kernel"));
         }
         KTimer t(c, "adj_tc_reduce");
-        launch_adj_tc_reduce(d, c->units, c->cb_off, c->partial, c->gsum, c->st);
+        launch_adj_tc_reduce(d, c->units, c->cb_off, c->partial, f16 ? c->yscale : nullptr, c->gsum, c->st);
         c->launches++;
         TRY(after_launch(c, "adjoint reduction"));
         *ks_out = 1;
@@ -693,10 +715,10 @@ void mem_destroy(mem_ctx* c) {
 
 mem_status mem_set_precision(mem_ctx* c, int32_t prec) {
     if (!c) return fail(nullptr, MEM_EINVAL, "null context");
-    if (prec < MEM_PREC_FP64_DIRECT || prec > MEM_PREC_BF16X3)
+    if (prec < MEM_PREC_FP64_DIRECT || prec > MEM_PREC_FP16X3)
         return fail(c, MEM_EINVAL, "unknown precision %d", prec);
-    if (prec == MEM_PREC_BF16X3 && !tc_shape_ok(c->N))
-        return fail(c, MEM_ENOTSUP, "BF16X3 form needs N = 64, 128 or a multiple of 256 (N = %d)", c->N);
+    if (is_tc(prec) && !tc_shape_ok(c->N))
+        return fail(c, MEM_ENOTSUP, "tensor-core forms need N = 64, 128 or a multiple of 256 (N = %d)", c->N);
     c->prec = prec;
     return ensure_buffers(c);
 }
@@ -712,12 +734,12 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
     if (!(cfg->dx > 0) || !(cfg->dy > 0)) return fail(nullptr, MEM_EINVAL, "pixel size must be > 0");
     if (!(cfg->G > 0) || !(cfg->lambda >= 0) || !std::isfinite(cfg->G) || !std::isfinite(cfg->lambda))
         return fail(nullptr, MEM_EINVAL, "need G > 0 and lambda >= 0");
-    if (cfg->precision < MEM_PREC_FP64_DIRECT || cfg->precision > MEM_PREC_BF16X3)
+    if (cfg->precision < MEM_PREC_FP64_DIRECT || cfg->precision > MEM_PREC_FP16X3)
         return fail(nullptr, MEM_EINVAL, "unknown precision %d", cfg->precision);
     if (cfg->image_mode != MEM_IMAGES_PER_CHANNEL && cfg->image_mode != MEM_IMAGE_SHARED)
         return fail(nullptr, MEM_EINVAL, "unknown image mode %d", cfg->image_mode);
-    if (cfg->precision == MEM_PREC_BF16X3 && !tc_shape_ok(N))
-        return fail(nullptr, MEM_ENOTSUP, "BF16X3 form needs N = 64, 128 or a multiple of 256 (N = %d)", N);
+    if (is_tc(cfg->precision) && !tc_shape_ok(N))
+        return fail(nullptr, MEM_ENOTSUP, "tensor-core forms need N = 64, 128 or a multiple of 256 (N = %d)", N);
     if (cfg->vis_offsets[0] != 0) return fail(nullptr, MEM_EINVAL, "vis_offsets[0] must be 0");
     for (int i = 0; i < C; ++i)
         if (cfg->vis_offsets[i + 1] < cfg->vis_offsets[i]) return fail(nullptr, MEM_EINVAL, "vis_offsets must not decrease");

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "internal.h"
 
@@ -203,10 +204,33 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
-// Instruction descriptor, kind::f16: D f32, A/B bf16, dense.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn_major, int b_mn_major) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) |
+// Instruction descriptor, kind::f16: D f32, A and B both bf16 (bf16 = 1) or
+// both f16 (bf16 = 0), dense.
+__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, int a_mn_major, int b_mn_major,
+                                                     int bf16) {
+    return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | ((uint32_t)a_mn_major << 15) |
            ((uint32_t)b_mn_major << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn_major, int b_mn_major) {
+    return idesc_f16kind(M, N, a_mn_major, b_mn_major, 1);
+}
+
+// Split x into f16 hi + lo with x ~= hi + lo (|x - hi - lo| <~ 2^-22 |x| in the
+// normal range; callers scale operands so that they stay in range).
+__device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    __half2 h = __floats2half2_rn(a, b);
+    float2 hf = __half22float2(h);
+    __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<uint32_t*>(&h);
+    lo = *reinterpret_cast<uint32_t*>(&l);
+}
+
+// 2^(14 - e) for the exponent e of x > 0 (x * scale in [2^14, 2^15)); 1 for x <= 0.
+__host__ __device__ __forceinline__ float pow2_scale_for(float x) {
+    if (!(x > 0.f)) return 1.f;
+    int e;
+    frexpf(x, &e);  // x = f 2^e, f in [0.5, 1)
+    return ldexpf(1.f, 15 - e);
 }
 
 // Split x into bf16 hi + lo with x ~= hi + lo (|x - hi - lo| <~ 2^-16 |x|).
@@ -216,6 +240,13 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uin
     __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
     hi = *reinterpret_cast<uint32_t*>(&h);
     lo = *reinterpret_cast<uint32_t*>(&l);
+}
+
+// Split into the 16-bit format of the tensor-core form (F16: f16, else bf16).
+template <bool F16>
+__device__ __forceinline__ void split16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    if (F16) split_f16x2(a, b, hi, lo);
+    else split_bf16x2(a, b, hi, lo);
 }
 
 }  // namespace msk

@@ -56,7 +56,7 @@ struct ImgSrc {
     int diff;             // operand is max(I + alpha d, G) - I, entropy as a difference
 };
 
-enum BFormat { BF_F32 = 0, BF_F64 = 1, BF_BF16X3 = 2 };
+enum BFormat { BF_F32 = 0, BF_F64 = 1, BF_BF16X3 = 2, BF_F16X3 = 3 };
 // FWD_VIS: write V.  FWD_RESID: write y = w (V - V^o), chi^2 partials.
 // FWD_CHI: chi^2 partials only.  FWD_CURV: 1/2 w |V|^2 partials.
 // FWD_DCHI: chi^2 change for an operand that is an image difference delta,
@@ -81,12 +81,20 @@ void launch_phase_prep(int64_t Z, const double* u, const double* v, double dx, d
                        uint64_t* pa, uint64_t* pb, cudaStream_t st);
 
 // B_c = A_c * img(c) for every channel in the requested format; entropy
-// partials S_i per (image, block) when ent_part != nullptr.  With cmean
-// (BF16X3 only) the planes hold B - c_m, c_m the column mean.
+// partials S_i per (image, block) when ent_part != nullptr.  The tensor-core
+// formats hold B - c_m (c_m the column mean from launch_colmean); F16X3 also
+// scales each channel by cscale[c] (a power of two, written here).
 void launch_prep(const DevData& d, const ImgSrc& src, int fmt, void* bout, double* ent_part,
-                 const float* cmean, cudaStream_t st);
-// Column means of B_c per channel into cmean[C][N].
-void launch_colmean(const DevData& d, const ImgSrc& src, float* cmean, cudaStream_t st);
+                 const float* cmean, const float* cmax, float* cscale, cudaStream_t st);
+// Column means of B_c per channel into cmean[C][N]; per 32-column block the
+// bound max|B| + |c_m| into cmax[C][ceil(N/32)].
+// psum (double) and pmax (float) hold colmean_tmp_count(N, C) entries each.
+void launch_colmean(const DevData& d, const ImgSrc& src, float* cmean, float* cmax, double* psum,
+                    float* pmax, cudaStream_t st);
+int colmean_tmp_count(int N, int C);
+__host__ __device__ inline int colmean_blocks(int N) { return (N + 31) / 32; }
+// yscale[0] = power-of-two scale for max|y| over 2*Z floats (part: 256 floats).
+void launch_absmax_scale(int64_t n, const float* y, float* part, float* yscale, cudaStream_t st);
 int prep_blocks(int N);
 
 void launch_fwd_direct(const DevData& d, int fp64, const VisTile* tiles, int n_tiles, const void* B,
@@ -98,13 +106,16 @@ int adj_direct_splits(const DevData& d, int num_sms);
 
 // Tensor-core forms.
 int fwd_tc_smem_bytes(int N);
-void launch_fwd_tc(const DevData& d, const VisTile* tiles, int n_tiles, const void* planes,
-                   const float* cmean, int mode, float2* yout, double* chi_part, int grid,
-                   uint64_t spin, int* status, cudaStream_t st);
+// f16 = 1: FP16X3 operands (planes scaled by cscale[c]); 0: BF16X3.
+void launch_fwd_tc(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
+                   const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,
+                   int grid, uint64_t spin, int* status, cudaStream_t st);
 int adj_tc_smem_bytes(int N);
 // units sorted by CTA: CTA b runs units [cta_unit_off[b], cta_unit_off[b+1]).
-void launch_adj_tc(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                   const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st);
+// f16 = 1: FP16X3 with y scaled by yscale[0] (partials carry the scale).
+void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
+                   const float2* y, const float* yscale, float* partial, uint64_t spin, int* status,
+                   cudaStream_t st);
 // Variant reading u, v (FP64, wavelengths) instead of the prepared phase
 // increments: the caller passes d.u, d.v, d.dx, d.dy; d.pa / d.pb are unused.
 void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
@@ -113,8 +124,9 @@ void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_uni
 void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partial, const float* beam,
                               float* out, cudaStream_t st);
 // Sum unit partials per channel (unit order) into gsum[C][N*N].
+// yscale (nullable): partials are divided by yscale[0].
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* unit_off_by_chan_blk,
-                          const float* partial, double* gsum, cudaStream_t st);
+                          const float* partial, const float* yscale, double* gsum, cudaStream_t st);
 
 // grad_i = sum_{c in image i} A_c * sum_k gsum[k][c] + lambda (1 + log(I/G)); optional projection.
 void launch_finalize(const DevData& d, const ImgSrc& src, const double* gsum, int ks, int projected,

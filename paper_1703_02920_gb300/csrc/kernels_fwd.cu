@@ -59,10 +59,14 @@ struct F2Shared {
     int abort;
 };
 
+// F16: FP16X3 operands (the image planes are scaled by cscale[channel], a
+// power of two undone in the epilogue); otherwise BF16X3.
+template <bool F16>
 __global__ void __launch_bounds__(F2_THREADS, 1)
     k_fwd_tc(DevData d, const VisTile* __restrict__ tiles, int n_tiles,
-             const __nv_bfloat16* __restrict__ planes, const float* __restrict__ cmean, int mode,
-             float2* __restrict__ yout, double* __restrict__ chi_part, uint64_t spin, int* status) {
+             const uint16_t* __restrict__ planes, const float* __restrict__ cmean,
+             const float* __restrict__ cscale, int mode, float2* __restrict__ yout,
+             double* __restrict__ chi_part, uint64_t spin, int* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ F2Shared S;
     const int N = d.N, c0 = N / 2;
@@ -100,7 +104,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
     if (warp == 4) {
         // ---------------------------------------------------------------- MMA
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(128, BN, 0, 0);
+            const uint32_t idesc = idesc_f16kind(128, BN, 0, 0, F16 ? 0 : 1);
             const uint32_t sbase = smem_u32(smem);
             const uint32_t lboB = (uint32_t)(BN / 8) * 128;
             uint32_t sc = 0, it = 0;
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             const uint32_t chunk_bytes = 2u * BN * TC_BK * 2;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int chan = tiles[t].chan;
-                const unsigned char* cbase = (const unsigned char*)(planes + (int64_t)chan * 2 * NN);
+                const unsigned char* cbase = (const unsigned char*)(planes + (int64_t)chan * 2 * NN);  // 16-bit elements
                 for (int mb = 0; mb < n_mb && ok; ++mb) {
                     for (int ks = 0; ks < nk; ++ks, ++sc) {
                         const int s = sc % F2_STAGES;
@@ -205,14 +209,14 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                         cf2 z[8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) z[q] = cmul(base, step[q]);
-                        split_bf16x2(z[0].x, z[1].x, rh.x, rl.x);
-                        split_bf16x2(z[2].x, z[3].x, rh.y, rl.y);
-                        split_bf16x2(z[4].x, z[5].x, rh.z, rl.z);
-                        split_bf16x2(z[6].x, z[7].x, rh.w, rl.w);
-                        split_bf16x2(z[0].y, z[1].y, ih.x, il.x);
-                        split_bf16x2(z[2].y, z[3].y, ih.y, il.y);
-                        split_bf16x2(z[4].y, z[5].y, ih.z, il.z);
-                        split_bf16x2(z[6].y, z[7].y, ih.w, il.w);
+                        split16x2<F16>(z[0].x, z[1].x, rh.x, rl.x);
+                        split16x2<F16>(z[2].x, z[3].x, rh.y, rl.y);
+                        split16x2<F16>(z[4].x, z[5].x, rh.z, rl.z);
+                        split16x2<F16>(z[6].x, z[7].x, rh.w, rl.w);
+                        split16x2<F16>(z[0].y, z[1].y, ih.x, il.x);
+                        split16x2<F16>(z[2].y, z[3].y, ih.y, il.y);
+                        split16x2<F16>(z[4].y, z[5].y, ih.z, il.z);
+                        split16x2<F16>(z[6].y, z[7].y, ih.w, il.w);
                     }
                     *(uint4*)(A + off) = rh;
                     *(uint4*)(A + off + 16) = ih;
@@ -256,6 +260,8 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                 const float D = (sh != 0.f) ? snb / sh : (float)N;
                 scomp = comp ? sh * D : ch * D;
             }
+            const float osc = F16 ? cscale[tl.chan] : 1.f;  // operand scale (power of two)
+            scomp *= osc;
             const float* cm = cmean + (int64_t)tl.chan * N;
             float s0 = 0.f, s1 = 0.f, c0s = 0.f, c1s = 0.f;  // compensated sums
             for (int mb = 0; mb < n_mb; ++mb, ++it) {
@@ -308,7 +314,8 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             }
             if (!ok) break;
             // even lane: (sum ReEx ReT, sum ImEx ReT); odd lane: (sum ReEx ImT, sum ImEx ImT)
-            const double p0 = (double)s0 + (double)c0s, p1 = (double)s1 + (double)c1s;
+            const double inv = 1.0 / (double)osc;
+            const double p0 = ((double)s0 + (double)c0s) * inv, p1 = ((double)s1 + (double)c1s) * inv;
             const double q0 = __shfl_xor_sync(0xffffffffu, p0, 1);
             const double q1 = __shfl_xor_sync(0xffffffffu, p1, 1);
             double chi = 0.0;
@@ -352,15 +359,21 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
 
 int fwd_tc_smem_bytes(int N) { return F2_STAGES * f2_stage_bytes(tc_bn(N)) + 1024; }
 
-void launch_fwd_tc(const DevData& d, const VisTile* tiles, int n_tiles, const void* planes,
-                   const float* cmean, int mode, float2* yout, double* chi_part, int grid,
-                   uint64_t spin, int* status, cudaStream_t st) {
+void launch_fwd_tc(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
+                   const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,
+                   int grid, uint64_t spin, int* status, cudaStream_t st) {
     if (n_tiles <= 0) return;
     const int smem = fwd_tc_smem_bytes(d.N);
-    cudaFuncSetAttribute(k_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (grid > n_tiles) grid = n_tiles;
-    k_fwd_tc<<<grid, F2_THREADS, smem, st>>>(d, tiles, n_tiles, (const __nv_bfloat16*)planes, cmean, mode,
-                                             yout, chi_part, spin, status);
+    if (f16) {
+        cudaFuncSetAttribute(k_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_fwd_tc<true><<<grid, F2_THREADS, smem, st>>>(d, tiles, n_tiles, (const uint16_t*)planes, cmean,
+                                                       cscale, mode, yout, chi_part, spin, status);
+    } else {
+        cudaFuncSetAttribute(k_fwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_fwd_tc<false><<<grid, F2_THREADS, smem, st>>>(d, tiles, n_tiles, (const uint16_t*)planes, cmean,
+                                                        cscale, mode, yout, chi_part, spin, status);
+    }
 }
 
 }  // namespace msk

@@ -90,40 +90,123 @@ __device__ __forceinline__ int64_t tc_plane_index(int n, int m, int N, int BN) {
 }
 
 // Column means c_m = (1/N) sum_n B[n][m] per channel (the operand of the
-// tensor-core forward is centred column by column, see k_fwd_tc).  Block:
-// 32 columns x 8 row groups, fixed summation order.
-__global__ void __launch_bounds__(256) k_colmean(DevData d, ImgSrc src, float* __restrict__ cmean) {
+// tensor-core forward is centred column by column, see k_fwd_tc), in two
+// stages with a fixed summation order.  Stage 1: block (column block of 32,
+// row block rb of N/COL_RB rows) -> partial sums and max |B| per column.
+constexpr int COL_RB = 16;
+
+__global__ void __launch_bounds__(256) k_colsum_part(DevData d, ImgSrc src, double* __restrict__ psum,
+                                                     float* __restrict__ pmax) {
     __shared__ double sh[8][33];
+    __shared__ float shm[8][33];
     const int N = d.N;
     const int64_t NN = (int64_t)N * N;
-    const int c = blockIdx.y;
+    const int c = blockIdx.z, rb = blockIdx.y;
     const int i = image_of(d, c);
     const int m = blockIdx.x * 32 + (threadIdx.x & 31);
     const int rg = threadIdx.x >> 5;
+    const int n0 = (int)((int64_t)N * rb / COL_RB), n1 = (int)((int64_t)N * (rb + 1) / COL_RB);
     double acc = 0.0;
+    float amax = 0.f;
     if (m < N) {
-        for (int n = rg; n < N; n += 8) {
+        for (int n = n0 + rg; n < n1; n += 8) {
             const int64_t p = (int64_t)n * N + m;
             double x = img_value(src, i, p, NN);
             if (src.diff) x -= src.f64[(int64_t)i * NN + p];
-            acc += (double)d.beam[(int64_t)c * NN + p] * x;
+            const double b = (double)d.beam[(int64_t)c * NN + p] * x;
+            acc += b;
+            amax = fmaxf(amax, (float)fabs(b));
         }
     }
     sh[rg][threadIdx.x & 31] = acc;
+    shm[rg][threadIdx.x & 31] = amax;
     __syncthreads();
     if (rg == 0 && m < N) {
         double t = 0.0;
-        for (int k = 0; k < 8; ++k) t += sh[k][threadIdx.x];
-        cmean[(int64_t)c * N + m] = (float)(t / N);
+        float mx = 0.f;
+        for (int k = 0; k < 8; ++k) {
+            t += sh[k][threadIdx.x];
+            mx = fmaxf(mx, shm[k][threadIdx.x]);
+        }
+        psum[((int64_t)c * COL_RB + rb) * N + m] = t;
+        pmax[((int64_t)c * COL_RB + rb) * N + m] = mx;
     }
 }
 
-void launch_colmean(const DevData& d, const ImgSrc& src, float* cmean, cudaStream_t st) {
-    k_colmean<<<dim3((d.N + 31) / 32, d.C), 256, 0, st>>>(d, src, cmean);
+// Stage 2: one block per channel: c_m, and per 32-column block the bound
+// max_n |B[n][m] - c_m| <= max |B| + |c_m| into cmax[C][ceil(N/32)].
+__global__ void __launch_bounds__(256) k_colsum_final(int N, const double* __restrict__ psum,
+                                                      const float* __restrict__ pmax,
+                                                      float* __restrict__ cmean, float* __restrict__ cmax) {
+    const int c = blockIdx.x;
+    for (int mb = threadIdx.x >> 5; mb < colmean_blocks(N); mb += 8) {
+        const int m = mb * 32 + (threadIdx.x & 31);
+        float bound = 0.f;
+        if (m < N) {
+            double t = 0.0;
+            float mx = 0.f;
+            for (int rb = 0; rb < COL_RB; ++rb) {
+                t += psum[((int64_t)c * COL_RB + rb) * N + m];
+                mx = fmaxf(mx, pmax[((int64_t)c * COL_RB + rb) * N + m]);
+            }
+            const float cm = (float)(t / N);
+            cmean[(int64_t)c * N + m] = cm;
+            bound = mx + fabsf(cm);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bound = fmaxf(bound, __shfl_down_sync(0xffffffffu, bound, o));
+        if ((threadIdx.x & 31) == 0) cmax[(int64_t)c * colmean_blocks(N) + mb] = bound;
+    }
+}
+
+void launch_colmean(const DevData& d, const ImgSrc& src, float* cmean, float* cmax, double* psum,
+                    float* pmax, cudaStream_t st) {
+    k_colsum_part<<<dim3(colmean_blocks(d.N), COL_RB, d.C), 256, 0, st>>>(d, src, psum, pmax);
+    k_colsum_final<<<d.C, 256, 0, st>>>(d.N, psum, pmax, cmean, cmax);
+}
+
+int colmean_tmp_count(int N, int C) { return COL_RB * N * C; }
+
+// Power-of-two scale of channel c from its column-block bounds.
+__device__ __forceinline__ float chan_scale(const float* cmax, int c, int nb) {
+    float mx = 0.f;
+    for (int k = 0; k < nb; ++k) mx = fmaxf(mx, cmax[(int64_t)c * nb + k]);
+    return pow2_scale_for(mx);
+}
+
+// max |y| over n floats: 256 block maxima, then one block forms the scale.
+__global__ void __launch_bounds__(256) k_absmax_part(int64_t n, const float* __restrict__ y,
+                                                     float* __restrict__ part) {
+    float mx = 0.f;
+    for (int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x; k < n; k += (int64_t)gridDim.x * 256)
+        mx = fmaxf(mx, fabsf(y[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    __shared__ float sh[8];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = sh[0];
+        for (int k = 1; k < 8; ++k) t = fmaxf(t, sh[k]);
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_absmax_final(const float* __restrict__ part, float* yscale) {
+    if (threadIdx.x != 0) return;
+    float t = 0.f;
+    for (int k = 0; k < 256; ++k) t = fmaxf(t, part[k]);
+    yscale[0] = pow2_scale_for(t);
+}
+
+void launch_absmax_scale(int64_t n, const float* y, float* part, float* yscale, cudaStream_t st) {
+    k_absmax_part<<<256, 256, 0, st>>>(n, y, part);
+    k_absmax_final<<<1, 32, 0, st>>>(part, yscale);
 }
 
 __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, void* bout,
-                                              double* ent_part, const float* __restrict__ cmean) {
+                                              double* ent_part, const float* __restrict__ cmean,
+                                              const float* __restrict__ cmax, float* cscale) {
     __shared__ double sh[8];
     const int N = d.N;
     const int64_t NN = (int64_t)N * N;
@@ -152,13 +235,25 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
         } else {
             int n = (int)(p / N), m = (int)(p % N);
             int BN = tc_bn(N);
-            float bf = (float)(b - (cmean ? (double)cmean[(int64_t)c * N + m] : 0.0));
-            __nv_bfloat16 hi = __float2bfloat16_rn(bf);
-            __nv_bfloat16 lo = __float2bfloat16_rn(bf - __bfloat162float(hi));
-            __nv_bfloat16* base = (__nv_bfloat16*)bout + (int64_t)c * 2 * NN;
-            int64_t q = tc_plane_index(n, m, N, BN);
-            base[q] = hi;
-            base[q + (int64_t)BN * TC_BK] = lo;
+            const double cb = b - (cmean ? (double)cmean[(int64_t)c * N + m] : 0.0);
+            const int64_t q = tc_plane_index(n, m, N, BN);
+            if (fmt == BF_BF16X3) {
+                const float bf = (float)cb;
+                __nv_bfloat16 hi = __float2bfloat16_rn(bf);
+                __nv_bfloat16 lo = __float2bfloat16_rn(bf - __bfloat162float(hi));
+                __nv_bfloat16* base = (__nv_bfloat16*)bout + (int64_t)c * 2 * NN;
+                base[q] = hi;
+                base[q + (int64_t)BN * TC_BK] = lo;
+            } else {
+                const float sc = chan_scale(cmax, c, colmean_blocks(N));
+                if (p == 0) cscale[c] = sc;
+                const float bf = (float)(cb * (double)sc);
+                __half hi = __float2half_rn(bf);
+                __half lo = __float2half_rn(bf - __half2float(hi));
+                __half* base = (__half*)bout + (int64_t)c * 2 * NN;
+                base[q] = hi;
+                base[q + (int64_t)BN * TC_BK] = lo;
+            }
         }
     }
     if (ent_part) {
@@ -171,9 +266,9 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
 int prep_blocks(int N) { return (int)(((int64_t)N * N + 255) / 256); }
 
 void launch_prep(const DevData& d, const ImgSrc& src, int fmt, void* bout, double* ent_part,
-                 const float* cmean, cudaStream_t st) {
+                 const float* cmean, const float* cmax, float* cscale, cudaStream_t st) {
     dim3 grid(prep_blocks(d.N), d.C);
-    k_prep<<<grid, 256, 0, st>>>(d, src, fmt, bout, ent_part, cmean);
+    k_prep<<<grid, 256, 0, st>>>(d, src, fmt, bout, ent_part, cmean, cmax, cscale);
 }
 
 // ---------------------------------------------------------------------------

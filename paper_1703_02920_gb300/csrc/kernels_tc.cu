@@ -68,10 +68,13 @@ struct AdjShared {
 
 // FROM_UV: phase increments reduced from u, v inside the producers instead of
 // read from the prepared arrays.
-template <bool FROM_UV>
+// F16: FP16X3 operands with y scaled by yscale[0] (a power of two, undone
+// when the partials are summed); otherwise BF16X3.
+template <bool FROM_UV, bool F16>
 __global__ void __launch_bounds__(ADJ_THREADS, 1)
     k_adj_tc(DevData d, const AdjUnit* __restrict__ units, const int* __restrict__ cta_unit_off,
-             const float2* __restrict__ y, float* __restrict__ partial, uint64_t spin, int* status) {
+             const float2* __restrict__ y, const float* __restrict__ yscale, float* __restrict__ partial,
+             uint64_t spin, int* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ AdjShared S;
     const int N = d.N, c0 = N / 2;
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
 
     if (warp == 4) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(128, BLK, 1, 1);
+            const uint32_t idesc = idesc_f16kind(128, BLK, 1, 1, F16 ? 0 : 1);
             const uint32_t sbase = smem_u32(smem);
             uint32_t sc = 0;
             bool ok = true;
@@ -159,6 +162,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
         const int ptid = threadIdx.x - 192;
         const int jj = ptid & 15;           // visibility within the stage
         const int ngA = R / 8, ngB = BLK / 8;
+        const float ysc = F16 ? yscale[0] : 1.f;
         uint32_t sc = 0;
         bool ok = true;
         for (int u = u0; u < u1 && ok; ++u) {
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             for (int ks = 0; ks < nst; ++ks, ++sc) {
                 const int s = sc % ADJ_STAGES;
                 const uint64_t pa = na, pb = nb;
-                const cf2 yv = {ny.x, ny.y};
+                const cf2 yv = {ny.x * ysc, ny.y * ysc};
                 const bool valid = (int64_t)ks * TCA_BK + jj < un.count;
                 fetch(ks + 1, na, nb, ny);
                 ok = __all_sync(0xffffffffu, mbar_wait(&S.empty[s], ((sc / ADJ_STAGES) & 1) ^ 1, spin,
@@ -226,14 +230,14 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                             cf2 z[8];
 #pragma unroll
                             for (int q = 0; q < 8; ++q) z[q] = cmul(base, sy[q]);
-                            split_bf16x2(z[0].x, z[1].x, rh.x, rl.x);
-                            split_bf16x2(z[2].x, z[3].x, rh.y, rl.y);
-                            split_bf16x2(z[4].x, z[5].x, rh.z, rl.z);
-                            split_bf16x2(z[6].x, z[7].x, rh.w, rl.w);
-                            split_bf16x2(z[0].y, z[1].y, ih.x, il.x);
-                            split_bf16x2(z[2].y, z[3].y, ih.y, il.y);
-                            split_bf16x2(z[4].y, z[5].y, ih.z, il.z);
-                            split_bf16x2(z[6].y, z[7].y, ih.w, il.w);
+                            split16x2<F16>(z[0].x, z[1].x, rh.x, rl.x);
+                            split16x2<F16>(z[2].x, z[3].x, rh.y, rl.y);
+                            split16x2<F16>(z[4].x, z[5].x, rh.z, rl.z);
+                            split16x2<F16>(z[6].x, z[7].x, rh.w, rl.w);
+                            split16x2<F16>(z[0].y, z[1].y, ih.x, il.x);
+                            split16x2<F16>(z[2].y, z[3].y, ih.y, il.y);
+                            split16x2<F16>(z[4].y, z[5].y, ih.z, il.z);
+                            split16x2<F16>(z[6].y, z[7].y, ih.w, il.w);
                         }
                         dst = A + ((jj >> 3) * ngA + g) * 128 + (jj & 7) * 16;
                         plane = a_plane;
@@ -247,14 +251,14 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                             cf2 z[8];
 #pragma unroll
                             for (int q = 0; q < 8; ++q) z[q] = cmul(base, cf2{sx[q].x, -sx[q].y});
-                            split_bf16x2(z[0].x, z[1].x, rh.x, rl.x);
-                            split_bf16x2(z[2].x, z[3].x, rh.y, rl.y);
-                            split_bf16x2(z[4].x, z[5].x, rh.z, rl.z);
-                            split_bf16x2(z[6].x, z[7].x, rh.w, rl.w);
-                            split_bf16x2(z[0].y, z[1].y, ih.x, il.x);
-                            split_bf16x2(z[2].y, z[3].y, ih.y, il.y);
-                            split_bf16x2(z[4].y, z[5].y, ih.z, il.z);
-                            split_bf16x2(z[6].y, z[7].y, ih.w, il.w);
+                            split16x2<F16>(z[0].x, z[1].x, rh.x, rl.x);
+                            split16x2<F16>(z[2].x, z[3].x, rh.y, rl.y);
+                            split16x2<F16>(z[4].x, z[5].x, rh.z, rl.z);
+                            split16x2<F16>(z[6].x, z[7].x, rh.w, rl.w);
+                            split16x2<F16>(z[0].y, z[1].y, ih.x, il.x);
+                            split16x2<F16>(z[2].y, z[3].y, ih.y, il.y);
+                            split16x2<F16>(z[4].y, z[5].y, ih.z, il.z);
+                            split16x2<F16>(z[6].y, z[7].y, ih.w, il.w);
                         }
                         dst = B + ((jj >> 3) * ngB + g) * 128 + (jj & 7) * 16;
                         plane = b_plane;
@@ -312,20 +316,29 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
     }
 }
 
-void launch_adj_tc(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                   const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st) {
+void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
+                   const float2* y, const float* yscale, float* partial, uint64_t spin, int* status,
+                   cudaStream_t st) {
     if (n_ctas <= 0) return;
     int smem = adj_tc_smem_bytes(d.N);
-    cudaFuncSetAttribute(k_adj_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_adj_tc<false><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, partial, spin, status);
+    if (f16) {
+        cudaFuncSetAttribute(k_adj_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_adj_tc<false, true><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, yscale, partial,
+                                                                 spin, status);
+    } else {
+        cudaFuncSetAttribute(k_adj_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_adj_tc<false, false><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, yscale, partial,
+                                                                  spin, status);
+    }
 }
 
 void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
                       const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st) {
     if (n_ctas <= 0) return;
     int smem = adj_tc_smem_bytes(d.N);
-    cudaFuncSetAttribute(k_adj_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_adj_tc<true><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, partial, spin, status);
+    cudaFuncSetAttribute(k_adj_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_adj_tc<true, false><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, nullptr, partial, spin,
+                                                             status);
 }
 
 // Single channel: out[p] = A[p] * (unit partials summed in unit order, FP64).
@@ -356,6 +369,7 @@ void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partia
 // gsum[c][N*N] (without the beam factor).
 __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __restrict__ cb_unit_off,
                                                        const float* __restrict__ partial,
+                                                       const float* __restrict__ yscale,
                                                        double* __restrict__ gsum) {
     const int N = d.N;
     const int64_t NN = (int64_t)N * N;
@@ -383,14 +397,15 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __r
         for (int k = 0; k < 8; ++k) two_sum_acc(s, comp, q[k]);
     }
     for (; u < u1; ++u) two_sum_acc(s, comp, __ldg(src + (int64_t)u * stride));
-    gsum[(int64_t)c * NN + p] = (double)s + (double)comp;
+    const double inv = yscale ? 1.0 / (double)yscale[0] : 1.0;
+    gsum[(int64_t)c * NN + p] = ((double)s + (double)comp) * inv;
 }
 
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* cb_unit_off,
-                          const float* partial, double* gsum, cudaStream_t st) {
+                          const float* partial, const float* yscale, double* gsum, cudaStream_t st) {
     (void)units;
     dim3 grid(prep_blocks(d.N), d.C);
-    k_adj_tc_reduce<<<grid, 256, 0, st>>>(d, cb_unit_off, partial, gsum);
+    k_adj_tc_reduce<<<grid, 256, 0, st>>>(d, cb_unit_off, partial, yscale, gsum);
 }
 
 }  // namespace msk

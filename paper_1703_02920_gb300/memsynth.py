@@ -21,7 +21,9 @@ from . import build as _build
 PREC_FP64_DIRECT = 0
 PREC_FP32_DIRECT = 1
 PREC_BF16X3 = 2
-PRECISIONS = {"fp64_direct": PREC_FP64_DIRECT, "fp32_direct": PREC_FP32_DIRECT, "bf16x3": PREC_BF16X3}
+PREC_FP16X3 = 3
+PRECISIONS = {"fp64_direct": PREC_FP64_DIRECT, "fp32_direct": PREC_FP32_DIRECT, "bf16x3": PREC_BF16X3,
+              "fp16x3": PREC_FP16X3}
 IMAGES_PER_CHANNEL = 0
 IMAGE_SHARED = 1
 

@@ -18,10 +18,10 @@ pytestmark = pytest.mark.gpu
 
 # The FP64 form computes in FP64 but returns visibilities and gradients as
 # float32 through the ABI, so it agrees to float32 rounding of its outputs.
-TOL_V = {"fp64_direct": 2e-7, "fp32_direct": 1e-5, "bf16x3": 1e-5}
-TOL_G = {"fp64_direct": 2e-7, "fp32_direct": 1e-4, "bf16x3": 1e-4}
-TOL_PHI = {"fp64_direct": 1e-11, "fp32_direct": 1e-6, "bf16x3": 1e-6}
-FORMS = ["fp64_direct", "fp32_direct", "bf16x3"]
+TOL_V = {"fp64_direct": 2e-7, "fp32_direct": 1e-5, "bf16x3": 1e-5, "fp16x3": 1e-5}
+TOL_G = {"fp64_direct": 2e-7, "fp32_direct": 1e-4, "bf16x3": 1e-4, "fp16x3": 1e-4}
+TOL_PHI = {"fp64_direct": 1e-11, "fp32_direct": 1e-6, "bf16x3": 1e-6, "fp16x3": 1e-6}
+FORMS = ["fp64_direct", "fp32_direct", "bf16x3", "fp16x3"]
 
 
 @pytest.fixture(scope="module")
@@ -133,7 +133,7 @@ def test_precision_switch_reuses_context(ms, oracle_mod):
     ds = _case(CASES[1])
     ctx = ms.Context(ds, precision="fp64_direct")
     ref = _oracle_vis(oracle_mod, ds, ds.truth)
-    for form in ["bf16x3", "fp32_direct", "fp64_direct", "bf16x3"]:
+    for form in ["bf16x3", "fp32_direct", "fp16x3", "fp64_direct", "bf16x3"]:
         ctx.set_precision(form)
         V = ctx.forward(torch.from_numpy(ds.truth).cuda()).cpu().numpy().astype(np.float64)
         assert _rel_max(V[:, 0] + 1j * V[:, 1], ref) <= TOL_V[form]

@@ -34,7 +34,7 @@ def solve_ref(oracle_mod):
     return ds, img, hist[0]
 
 
-@pytest.mark.parametrize("form", ["fp64_direct", "bf16x3", "fp32_direct"])
+@pytest.mark.parametrize("form", ["fp64_direct", "bf16x3", "fp16x3", "fp32_direct"])
 def test_solve_matches_oracle(ms, solve_ref, form):
     import torch
     ds, ref_img, ref_hist = solve_ref
