@@ -205,14 +205,13 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    # ---- device-timed region: CUDA events on the context stream per step, L2 flushed between steps
+    # ---- device-timed region: CUDA events on the context stream per step, L2
+    # flushed between steps; each step replays the captured CUDA graph
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = ctx.launches()
-    ctx.profile(True)
-    ctx.profile_read()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.zero_()
@@ -224,8 +223,6 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     launches = ctx.launches() - launches0
-    kprof = ctx.profile_read()
-    ctx.profile(False)
     ctx.sync()
     ms = [a.elapsed_time(b) for a, b in ev]
     ms_step = sum(ms) / len(ms)
@@ -234,6 +231,16 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
     value = units * world / (ms_step * 1e-3)
+
+    # ---- per-kernel durations: the same steps again with every launch bracketed
+    # by CUDA events on the context stream (direct launches, no graph)
+    ctx.profile(True)
+    ctx.profile_read()
+    for k in range(args.steps):
+        flush.zero_()
+        step()
+    kprof = ctx.profile_read()
+    ctx.profile(False)
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
     himg = torch.from_numpy(np.maximum(ds.truth, ds.G).astype(np.float32)).pin_memory().numpy()

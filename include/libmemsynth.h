@@ -169,6 +169,12 @@ mem_status mem_solve(mem_ctx *ctx, float *image_dev_inout, int32_t n_iter,
  * reported a bounded-wait timeout or a CUDA error occurred. */
 mem_status mem_sync(mem_ctx *ctx);
 
+/* CUDA graphs (default on): every repeated launch sequence (objective +
+ * gradient for given image / gradient pointers, and the solver's evaluation,
+ * curvature and line-search probe sequences) is captured once, on a private
+ * stream, and replayed on the context stream.  Disabled while profiling. */
+mem_status mem_use_graphs(mem_ctx *ctx, int32_t enable);
+
 /* Kernel launches issued by ctx since creation (for launch accounting). */
 int64_t mem_launch_count(const mem_ctx *ctx);
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -285,6 +286,19 @@ struct mem_ctx {
     float* partial = nullptr;
     int* dstatus = nullptr;
     float* stage = nullptr;  // host-call staging (image, gradient)
+
+    // CUDA graphs: each repeated launch sequence is captured once (on a private
+    // stream: the legacy default stream cannot be captured) and replayed on st
+    struct GraphSlot {
+        const void* k1 = nullptr;
+        const void* k2 = nullptr;
+        int k3 = -1, prec = -1;
+        int64_t nlaunch = 0;
+        cudaGraphExec_t exec = nullptr;
+    };
+    bool graphs = true;
+    cudaStream_t cap_st = nullptr;
+    GraphSlot g_objgrad, g_solve_objgrad, g_solve_curv, g_solve_probe;
 
     // optional per-kernel timing (CUDA events on the context stream)
     bool profiling = false;
@@ -628,6 +642,63 @@ mem_status run_objgrad(mem_ctx* c, const ImgSrc& src, int projected, float* out3
     return after_launch(c, "gradient assembly");
 }
 
+void drop_graph(mem_ctx::GraphSlot& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = mem_ctx::GraphSlot();
+}
+
+void drop_graphs(mem_ctx* c) {
+    drop_graph(c->g_objgrad);
+    drop_graph(c->g_solve_objgrad);
+    drop_graph(c->g_solve_curv);
+    drop_graph(c->g_solve_probe);
+}
+
+// Run `body` (kernel launches on c->st only) through the graph slot: replay
+// when the slot was captured for the same keys, else capture and replay.
+// Buffers must already exist (no allocation inside a capture).
+mem_status graphed(mem_ctx* c, mem_ctx::GraphSlot& g, const void* k1, const void* k2, int k3,
+                   const std::function<mem_status()>& body) {
+    if (!c->graphs || c->profiling) return body();
+    if (!(g.exec && g.k1 == k1 && g.k2 == k2 && g.k3 == k3 && g.prec == c->prec)) {
+        drop_graph(g);
+        if (!c->cap_st) CK(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking), "capture stream");
+        cudaStream_t user = c->st;
+        c->st = c->cap_st;
+        const int64_t l0 = c->launches;
+        cudaError_t e = cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            c->st = user;
+            return cuda_fail(c, e, "begin capture");
+        }
+        mem_status s = body();
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(c->cap_st, &graph);
+        c->st = user;
+        const int64_t n = c->launches - l0;
+        c->launches = l0;
+        if (s != MEM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.exec = nullptr;
+            return cuda_fail(c, e, "graph instantiate");
+        }
+        g.k1 = k1;
+        g.k2 = k2;
+        g.k3 = k3;
+        g.prec = c->prec;
+        g.nlaunch = n;
+    }
+    CK(cudaGraphLaunch(g.exec, c->st), "graph launch");
+    c->launches += g.nlaunch;
+    return MEM_OK;
+}
+
 mem_status read_scalars(mem_ctx* c, std::vector<double>& out) {
     out.resize(3 + 3 * (size_t)c->n_images);
     CK(cudaMemcpyAsync(out.data(), c->scal, out.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st),
@@ -701,9 +772,18 @@ int32_t mem_profile_read(mem_ctx* c, int32_t max_kernels, char* names, double* m
     return i;
 }
 
+mem_status mem_use_graphs(mem_ctx* c, int32_t enable) {
+    if (!c) return fail(nullptr, MEM_EINVAL, "null context");
+    c->graphs = enable != 0;
+    if (!c->graphs) drop_graphs(c);
+    return MEM_OK;
+}
+
 void mem_destroy(mem_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->st);
+    drop_graphs(c);
+    if (c->cap_st) cudaStreamDestroy(c->cap_st);
     for (auto& k : c->kev) {
         cudaEventDestroy(k.a);
         cudaEventDestroy(k.b);
@@ -720,6 +800,7 @@ mem_status mem_set_precision(mem_ctx* c, int32_t prec) {
     if (is_tc(prec) && !tc_shape_ok(c->N))
         return fail(c, MEM_ENOTSUP, "tensor-core forms need N = 64, 128 or a multiple of 256 (N = %d)", c->N);
     c->prec = prec;
+    drop_graphs(c);
     return ensure_buffers(c);
 }
 
@@ -907,7 +988,9 @@ mem_status mem_objective_grad(mem_ctx* c, const float* image_dev, float* grad_de
                               double* out3_host) {
     if (!c || !image_dev) return fail(c, MEM_EINVAL, "null argument");
     ImgSrc src{image_dev, nullptr, nullptr, nullptr, c->G, 0};
-    TRY(run_objgrad(c, src, projected, grad_dev, nullptr, nullptr));
+    TRY(ensure_buffers(c));
+    TRY(graphed(c, c->g_objgrad, image_dev, grad_dev, projected ? 1 : 0,
+                [&]() { return run_objgrad(c, src, projected, grad_dev, nullptr, nullptr); }));
     if (out3_host) {
         std::vector<double> sc;
         TRY(read_scalars(c, sc));
@@ -965,7 +1048,8 @@ mem_status mem_solve(mem_ctx* c, float* image_dev_inout, int32_t n_iter, mem_sol
 
     auto objgrad = [&]() -> mem_status {
         ImgSrc src{nullptr, c->I64, nullptr, nullptr, c->G, 0};
-        TRY(run_objgrad(c, src, 1, nullptr, c->gf64, c->g64));
+        TRY(graphed(c, c->g_solve_objgrad, c->I64, c->gf64, 1,
+                    [&]() { return run_objgrad(c, src, 1, nullptr, c->gf64, c->g64); }));
         TRY(read_scalars(c, sc));
         for (int i = 0; i < NI; ++i) {
             phi[i] = sc[3 + 3 * i];
@@ -1047,7 +1131,8 @@ mem_status mem_solve(mem_ctx* c, float* image_dev_inout, int32_t n_iter, mem_sol
         // quadratic model of chi^2 along d: curvature sum w |F(A d)|^2
         {
             ImgSrc src{nullptr, c->d64, nullptr, nullptr, c->G, 0};
-            TRY(run_forward(c, src, FWD_CURV, false, nullptr));
+            TRY(graphed(c, c->g_solve_curv, c->d64, nullptr, FWD_CURV,
+                        [&]() { return run_forward(c, src, FWD_CURV, false, nullptr); }));
             TRY(read_scalars(c, sc));
         }
         std::vector<LineSearch> ls(NI);
@@ -1080,7 +1165,8 @@ mem_status mem_solve(mem_ctx* c, float* image_dev_inout, int32_t n_iter, mem_sol
             // scales with the step, not with Phi
             ImgSrc src{nullptr, c->I64, c->d64, c->alpha, c->G, 1};
             void* ybuf = c->prec == MEM_PREC_FP64_DIRECT ? (void*)c->y64 : (void*)c->y32;
-            TRY(run_forward(c, src, FWD_DCHI, true, ybuf));
+            TRY(graphed(c, c->g_solve_probe, c->I64, c->d64, FWD_DCHI,
+                        [&]() { return run_forward(c, src, FWD_DCHI, true, ybuf); }));
             TRY(read_scalars(c, sc));
             for (int i = 0; i < NI; ++i)
                 if (active[i] && ls[i].running()) ls[i].feed(phi[i] + sc[3 + 3 * i]);

@@ -54,7 +54,7 @@ _LIB = None
 EXPORTS = ["mem_create", "mem_destroy", "mem_last_error", "mem_status_string", "mem_set_precision",
            "mem_num_vis", "mem_num_images", "mem_forward", "mem_adjoint", "mem_objective_grad",
            "mem_objective_grad_host", "mem_scalars_dev", "mem_solve", "mem_sync", "mem_launch_count",
-           "mem_profile", "mem_profile_read", "mem_adjoint_noalloc"]
+           "mem_profile", "mem_profile_read", "mem_adjoint_noalloc", "mem_use_graphs"]
 
 
 def library_path() -> str:
@@ -108,6 +108,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.mem_profile.restype = ctypes.c_int
     lib.mem_profile_read.argtypes = [P, I32, ctypes.c_char_p, DP, ctypes.POINTER(ctypes.c_int64)]
     lib.mem_profile_read.restype = I32
+    lib.mem_use_graphs.argtypes = [P, I32]
+    lib.mem_use_graphs.restype = ctypes.c_int
     lib.mem_adjoint_noalloc.argtypes = [I32, D, D, I64, P, P, P, P, P, V]
     lib.mem_adjoint_noalloc.restype = ctypes.c_int
     _LIB = lib
@@ -210,6 +212,10 @@ def mem_adjoint_noalloc(n, dx, dy, u_dev, v_dev, y_dev, pb_dev, img_dev, stream=
     st = ctypes.c_void_p(0 if stream is None else int(stream))
     _check(load().mem_adjoint_noalloc(int(n), float(dx), float(dy), nv, _ptr(u_dev), _ptr(v_dev),
                                       _ptr(y_dev), _ptr(pb_dev), _ptr(img_dev), st))
+
+
+def mem_use_graphs(ctx, enable: bool):
+    _check(load().mem_use_graphs(ctx, int(bool(enable))), ctx)
 
 
 def mem_profile(ctx, enable: bool):
