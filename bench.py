@@ -5,10 +5,14 @@ and operand preparation, forward operator with fused residual / chi^2,
 adjoint (chi^2 gradient), entropy, gradient assembly and projection.  The
 metric is vis*pixel/s = Z * N^2 * steps / s.  Default workload: the
 256 x 256, 999,600-visibility single-channel data set (50 antennas, 1 km
-disk, 816 Earth-rotation dumps), split-BF16 tensor-core form.
+disk, 816 Earth-rotation dumps), split-FP16 (3-term) tensor-core form, tile
+shapes picked by the library's autotuner before the timed region.  Beside
+it: a fixed-iteration MEM solve timed in the same form and in the FP64
+direct form.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config 1..5] [--precision bf16x3|fp32_direct|fp64_direct]
+                  [--config 1..5] [--precision fp16x3|bf16x3|fp32_direct|fp64_direct]
+                  [--solve-iters I] [--no-solve]
 
 --impl reference times the FP64 CPU oracle on this machine's host cores on a
 bounded sample of the same workload (the paper's method as plainly stated).
@@ -167,7 +171,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 5])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "fp32_direct", "fp64_direct"])
+    ap.add_argument("--precision", default="fp16x3", choices=["bf16x3", "fp16x3", "fp32_direct", "fp64_direct"])
+    ap.add_argument("--solve-iters", type=int, default=4)
+    ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -201,6 +207,10 @@ def main():
     def step():
         memsynth.mem_objective_grad(ctx.handle, img, grad, 0, want_scalars=False)
 
+    tiles = None
+    if args.precision in ("bf16x3", "fp16x3"):
+        bn, fs, ast = ctx.autotune(img)
+        tiles = {"fwd_cols": bn, "fwd_stages": fs, "adj_stages": ast}
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -270,8 +280,8 @@ def main():
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
                     "note": f"{name}: {avg_ms:.3f} ms/launch, 4 algorithmic flops per vis*pixel "
-                            f"(12 executed in 3-term BF16: executed {3 * achieved:.0f} TFLOP/s); "
-                            f"peak = {src} sustained bf16"}
+                            f"(12 executed in the 3-term split: executed {3 * achieved:.0f} TFLOP/s); "
+                            f"peak = {src} sustained bf16 (fp16 dense rate is the same)"}
         else:
             roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
                     "frac": None, "traffic": None, "note": f"{name}: {avg_ms:.3f} ms/launch"}
@@ -280,6 +290,26 @@ def main():
                 "frac": None, "traffic": None, "note": name}
     kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1],
                    "share": v[0] / max(sum(x[0] for x in kprof.values()), 1e-30)} for k, v in kprof.items()}
+
+    # ---- MEM solve from I = G: a few CG iterations in this form and in the
+    # FP64 direct form (same algorithm, same start)
+    solve = None
+    if not args.no_solve and args.solve_iters > 0:
+        I0 = torch.full_like(img, float(ds.G))
+        solve = {"iterations": args.solve_iters}
+        for key, prec in (("form", args.precision), ("fp64", "fp64_direct")):
+            sctx = ctx if prec == args.precision else memsynth.Context(ds, precision=prec)
+            sctx.solve(I0, 1)  # warm-up (graph capture, buffers)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, rep, _ = sctx.solve(I0, args.solve_iters)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            solve[key] = {"precision": prec, "s": dt, "ms_per_iter": dt * 1e3 / max(rep.iterations, 1),
+                          "evaluations": rep.evaluations, "phi": rep.phi}
+            if sctx is not ctx:
+                sctx.close()
+        solve["speedup_vs_fp64"] = solve["fp64"]["s"] / solve["form"]["s"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -295,12 +325,12 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.config], "precision": args.precision,
                            "image": f"{N}x{N}", "visibilities": Z, "parallelism": f"replicas x{world}",
-                           "l2": "flushed between timed steps (256 MB write)"},
+                           "l2": "flushed between timed steps (256 MB write)", "tiles": tiles},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(img.numel() * 4),
                         "d2h_bytes_per_step": int(img.numel() * 4 + 24)},
                 "gpu_launches": launches,
                 "roofline": roof, "kernels": kernels,
-                "clocks": clk.summary(), "cpu_baseline": cpu}
+                "clocks": clk.summary(), "cpu_baseline": cpu, "solve": solve}
         print(json.dumps(line))
     ctx.close()
     return 0

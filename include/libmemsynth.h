@@ -169,6 +169,26 @@ mem_status mem_solve(mem_ctx *ctx, float *image_dev_inout, int32_t n_iter,
  * reported a bounded-wait timeout or a CUDA error occurred. */
 mem_status mem_sync(mem_ctx *ctx);
 
+/* Autotune the tensor-core tiling on this context's data (a no-op for the
+ * direct forms): forward image column block (128 or 256 columns when N >=
+ * 256) and pipeline depth (3 or 4 stages), adjoint pipeline depth (2 or 3);
+ * each candidate is timed over `reps` (0: 3) objective + gradient
+ * evaluations at image_dev with per-kernel CUDA events.  The choice is kept
+ * in the context and appended to a cache file (MEMSYNTH_TUNE_CACHE, default
+ * $HOME/.cache/libmemsynth_tune.txt) that mem_create reads back for the same
+ * device, N, visibility-count octave, channel count and form.  choice_out
+ * (nullable, host): 3 ints (column block, forward stages, adjoint stages). */
+mem_status mem_autotune(mem_ctx *ctx, const float *image_dev, int32_t reps, int32_t *choice_out);
+
+/* Set the tensor-core tiling explicitly: the column block a multiple of 32
+ * that divides N (at most 256), forward stages 3 or 4, adjoint stages 2 or 3.  Waits for the context's stream.  MEM_EINVAL
+ * for a direct form or an invalid shape. */
+mem_status mem_set_tiling(mem_ctx *ctx, int32_t fwd_cols, int32_t fwd_stages, int32_t adj_stages);
+
+/* The tiling in use (3 ints, host): column block, forward stages, adjoint
+ * stages.  The direct forms report the defaults, which they do not use. */
+mem_status mem_tiling(const mem_ctx *ctx, int32_t *out3);
+
 /* CUDA graphs (default on): every repeated launch sequence (objective +
  * gradient for given image / gradient pointers, and the solver's evaluation,
  * curvature and line-search probe sequences) is captured once, on a private

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <sys/stat.h>
+
 #include "../../include/libmemsynth.h"
 #include "internal.h"
 
@@ -300,6 +302,10 @@ struct mem_ctx {
     cudaStream_t cap_st = nullptr;
     GraphSlot g_objgrad, g_solve_objgrad, g_solve_curv, g_solve_probe;
 
+    // tensor-core tiling (autotuned)
+    int fwd_bn = 0, fwd_stages = 4, adj_stages = 3;
+    std::string gpu_name;
+
     // optional per-kernel timing (CUDA events on the context stream)
     bool profiling = false;
     struct KEv {
@@ -333,6 +339,9 @@ struct mem_ctx {
         d.off = doff;
         d.dx = dx;
         d.dy = dy;
+        d.fwd_bn = fwd_bn;
+        d.fwd_stages = fwd_stages;
+        d.adj_stages = adj_stages;
         return d;
     }
 };
@@ -715,6 +724,78 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 void msk::set_global_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Autotuner.  Candidates: forward image column block BN in {128, 256} (N >=
+// 256; the operand planes are laid out per BN) and pipeline depth {3, 4};
+// adjoint pipeline depth {2, 3}.  Each candidate is timed with per-kernel
+// CUDA events over a few full objective + gradient evaluations of the
+// context's own data; the fastest is kept and recorded in a cache file
+// (MEMSYNTH_TUNE_CACHE, default $HOME/.cache/libmemsynth_tune.txt) keyed by
+// device name, N, log2 of the visibility count, channel count and form.
+// ---------------------------------------------------------------------------
+std::string tune_key(const mem_ctx* c) {
+    int zb = 0;
+    while (((int64_t)1 << (zb + 1)) <= std::max<int64_t>(c->Z, 1)) ++zb;
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s|N=%d|z=%d|C=%d|prec=%d", c->gpu_name.c_str(), c->N, zb, c->C, c->prec);
+    std::string k = buf;
+    for (char& ch : k)
+        if (ch == ' ') ch = '_';
+    return k;
+}
+
+std::string tune_path() {
+    const char* p = std::getenv("MEMSYNTH_TUNE_CACHE");
+    if (p && *p) return p;
+    const char* h = std::getenv("HOME");
+    return std::string(h ? h : ".") + "/.cache/libmemsynth_tune.txt";
+}
+
+bool tune_valid(const mem_ctx* c, int bn, int fs, int as) {
+    // the epilogue reduces 32-column pairs of 16-column chunks
+    if (bn < 32 || bn > 256 || c->N % bn != 0 || bn % 32 != 0) return false;
+    if (!(fs == 3 || fs == 4) || !(as == 2 || as == 3)) return false;
+    return fwd_tc_smem_bytes(bn, fs) <= 227 * 1024 && adj_tc_smem_bytes(c->N, as) <= 227 * 1024;
+}
+
+void tune_load(mem_ctx* c) {
+    FILE* f = std::fopen(tune_path().c_str(), "r");
+    if (!f) return;
+    const std::string key = tune_key(c);
+    char k[256];
+    int bn, fs, as;
+    while (std::fscanf(f, "%255s %d %d %d", k, &bn, &fs, &as) == 4)
+        if (key == k && tune_valid(c, bn, fs, as)) {
+            c->fwd_bn = bn;
+            c->fwd_stages = fs;
+            c->adj_stages = as;
+        }
+    std::fclose(f);
+}
+
+void tune_store(const mem_ctx* c) {
+    const std::string path = tune_path();
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) {
+        const std::string dir = path.substr(0, slash);
+        std::string cmd;  // create the directory without a shell
+        for (size_t i = 1; i <= dir.size(); ++i)
+            if (i == dir.size() || dir[i] == '/') {
+                std::string sub = dir.substr(0, i);
+                mkdir(sub.c_str(), 0755);
+            }
+    }
+    FILE* f = std::fopen(path.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d %d\n", tune_key(c).c_str(), c->fwd_bn, c->fwd_stages, c->adj_stages);
+    std::fclose(f);
+}
+
+}  // namespace
+
+
 extern "C" {
 
 const char* mem_status_string(mem_status s) {
@@ -770,6 +851,92 @@ int32_t mem_profile_read(mem_ctx* c, int32_t max_kernels, char* names, double* m
     }
     c->kacc.clear();
     return i;
+}
+
+mem_status mem_autotune(mem_ctx* c, const float* image_dev, int32_t reps, int32_t* choice_out) {
+    if (!c || !image_dev) return fail(c, MEM_EINVAL, "null argument");
+    if (!is_tc(c->prec)) return MEM_OK;  // nothing to tune for the direct forms
+    if (reps <= 0) reps = 3;
+    TRY(ensure_buffers(c));
+    const bool prof0 = c->profiling;
+    c->profiling = true;
+    auto time_kernel = [&](const char* name, double* best) -> mem_status {
+        ImgSrc src{image_dev, nullptr, nullptr, nullptr, c->G, 0};
+        TRY(run_objgrad(c, src, 0, nullptr, nullptr, nullptr));  // warm-up
+        mem_profile_read(c, 0, nullptr, nullptr, nullptr);
+        for (int r = 0; r < reps; ++r) TRY(run_objgrad(c, src, 0, nullptr, nullptr, nullptr));
+        char names[32 * 32];
+        double ms[32];
+        int64_t cnt[32];
+        const int n = mem_profile_read(c, 32, names, ms, cnt);
+        *best = 1e300;
+        for (int i = 0; i < n; ++i)
+            if (std::strcmp(names + 32 * i, name) == 0) *best = ms[i] / (double)cnt[i];
+        return check_status(c);
+    };
+    std::vector<int> bns;
+    if (c->N >= 256) bns = {256, 128};
+    else bns = {c->N};
+    int best_bn = c->fwd_bn, best_fs = c->fwd_stages, best_as = c->adj_stages;
+    double best_f = 1e300, best_a = 1e300;
+    mem_status st = MEM_OK;
+    for (int bn : bns)
+        for (int fs : {4, 3}) {
+            if (!tune_valid(c, bn, fs, c->adj_stages)) continue;
+            c->fwd_bn = bn;
+            c->fwd_stages = fs;
+            double t = 0;
+            if ((st = time_kernel("fwd_tc", &t)) != MEM_OK) break;
+            if (t < best_f) {
+                best_f = t;
+                best_bn = bn;
+                best_fs = fs;
+            }
+        }
+    c->fwd_bn = best_bn;
+    c->fwd_stages = best_fs;
+    for (int as : {3, 2}) {
+        if (st != MEM_OK || !tune_valid(c, c->fwd_bn, c->fwd_stages, as)) continue;
+        c->adj_stages = as;
+        double t = 0;
+        if ((st = time_kernel("adj_tc", &t)) != MEM_OK) break;
+        if (t < best_a) {
+            best_a = t;
+            best_as = as;
+        }
+    }
+    c->adj_stages = best_as;
+    c->profiling = prof0;
+    drop_graphs(c);
+    if (st != MEM_OK) return st;
+    tune_store(c);
+    if (choice_out) {
+        choice_out[0] = c->fwd_bn;
+        choice_out[1] = c->fwd_stages;
+        choice_out[2] = c->adj_stages;
+    }
+    return MEM_OK;
+}
+
+mem_status mem_set_tiling(mem_ctx* c, int32_t fwd_cols, int32_t fwd_stages, int32_t adj_stages) {
+    if (!c) return MEM_EINVAL;
+    if (!is_tc(c->prec)) return fail(c, MEM_EINVAL, "tiling applies to the tensor-core forms only");
+    if (!tune_valid(c, fwd_cols, fwd_stages, adj_stages))
+        return fail(c, MEM_EINVAL, "tiling: column block must divide N (16..256), stages 3|4 and 2|3");
+    TRY(mem_sync(c));
+    c->fwd_bn = fwd_cols;
+    c->fwd_stages = fwd_stages;
+    c->adj_stages = adj_stages;
+    drop_graphs(c);
+    return MEM_OK;
+}
+
+mem_status mem_tiling(const mem_ctx* c, int32_t* out3) {
+    if (!c || !out3) return MEM_EINVAL;
+    out3[0] = c->fwd_bn;
+    out3[1] = c->fwd_stages;
+    out3[2] = c->adj_stages;
+    return MEM_OK;
 }
 
 mem_status mem_use_graphs(mem_ctx* c, int32_t enable) {
@@ -862,6 +1029,8 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
         return bail(fail(nullptr, MEM_ECUDA, "libmemsynth is built for sm_103a (GB300); device is sm_%d%d",
                          prop.major, prop.minor));
     c->num_sms = prop.multiProcessorCount;
+    c->gpu_name = prop.name;
+    c->fwd_bn = tc_bn(N);
 
     const size_t NN = (size_t)N * N;
     mem_status s;
@@ -922,6 +1091,7 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
         g_last_error = c->err;
         return bail(MEM_ECUDA);
     }
+    if (is_tc(c->prec)) tune_load(c);
     if ((s = ensure_buffers(c)) != MEM_OK) {
         g_last_error = c->err;
         return bail(s);

@@ -43,6 +43,10 @@ struct DevData {
     const float* beam;   // C*N*N
     const int64_t* off;  // C+1
     double dx, dy;       // pixel size (radians)
+    // tensor-core tiling chosen by the autotuner (defaults: tc_bn(N), 4, 3)
+    int fwd_bn;          // forward image column block (divides N, <= 256)
+    int fwd_stages;      // forward pipeline depth (3 or 4)
+    int adj_stages;      // adjoint pipeline depth (2 or 3)
 };
 
 // Where pixel values come from: the caller's FP32 image, or the solver's FP64
@@ -105,12 +109,12 @@ void launch_adj_direct(const DevData& d, int fp64, const void* y, double* gsum, 
 int adj_direct_splits(const DevData& d, int num_sms);
 
 // Tensor-core forms.
-int fwd_tc_smem_bytes(int N);
+int fwd_tc_smem_bytes(int BN, int stages);
 // f16 = 1: FP16X3 operands (planes scaled by cscale[c]); 0: BF16X3.
 void launch_fwd_tc(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
                    const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,
                    int grid, uint64_t spin, int* status, cudaStream_t st);
-int adj_tc_smem_bytes(int N);
+int adj_tc_smem_bytes(int N, int stages);
 // units sorted by CTA: CTA b runs units [cta_unit_off[b], cta_unit_off[b+1]).
 // f16 = 1: FP16X3 with y scaled by yscale[0] (partials carry the scale).
 void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* cta_unit_off, int n_ctas,

@@ -30,7 +30,7 @@ namespace msk {
 
 namespace {
 
-constexpr int F2_STAGES = 4;
+constexpr int F2_MAX_STAGES = 4;
 constexpr int F2_THREADS = 448;
 constexpr int F2_APLANE = 128 * TC_BK * 2;  // bytes of one A plane (hi or lo), 8 KB
 constexpr int F2_ABYTES = 2 * F2_APLANE;
@@ -49,9 +49,9 @@ __device__ __forceinline__ cf2 cis_neg(uint64_t p) {
 }
 
 struct F2Shared {
-    uint64_t full[F2_STAGES];   // producer warps (8 arrivals)
-    uint64_t bfull[F2_STAGES];  // image operand bulk copy (transaction bytes)
-    uint64_t empty[F2_STAGES];  // MMA completion (tcgen05.commit)
+    uint64_t full[F2_MAX_STAGES];   // producer warps (8 arrivals)
+    uint64_t bfull[F2_MAX_STAGES];  // image operand bulk copy (transaction bytes)
+    uint64_t empty[F2_MAX_STAGES];  // MMA completion (tcgen05.commit)
     uint64_t tfull[2];
     uint64_t tempty[2];         // 4 epilogue warps
     uint64_t drain;
@@ -61,7 +61,8 @@ struct F2Shared {
 
 // F16: FP16X3 operands (the image planes are scaled by cscale[channel], a
 // power of two undone in the epilogue); otherwise BF16X3.
-template <bool F16>
+// F2_STAGES: depth of the shared-memory pipeline (autotuned).
+template <bool F16, int F2_STAGES>
 __global__ void __launch_bounds__(F2_THREADS, 1)
     k_fwd_tc(DevData d, const VisTile* __restrict__ tiles, int n_tiles,
              const uint16_t* __restrict__ planes, const float* __restrict__ cmean,
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ F2Shared S;
     const int N = d.N, c0 = N / 2;
-    const int BN = tc_bn(N);
+    const int BN = d.fwd_bn;
     const int n_mb = N / BN, nk = N / TC_BK;
     const int stage_bytes = f2_stage_bytes(BN);
     const uint32_t tcols = f2_tmem_cols(BN);
@@ -357,22 +358,30 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
 
 }  // namespace
 
-int fwd_tc_smem_bytes(int N) { return F2_STAGES * f2_stage_bytes(tc_bn(N)) + 1024; }
+int fwd_tc_smem_bytes(int BN, int stages) { return stages * f2_stage_bytes(BN) + 1024; }
+
+template <bool F16, int STAGES>
+static void launch_fwd_variant(const DevData& d, const VisTile* tiles, int n_tiles, const void* planes,
+                               const float* cmean, const float* cscale, int mode, float2* yout,
+                               double* chi_part, int grid, uint64_t spin, int* status, cudaStream_t st) {
+    const int smem = fwd_tc_smem_bytes(d.fwd_bn, STAGES);
+    cudaFuncSetAttribute(k_fwd_tc<F16, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_fwd_tc<F16, STAGES><<<grid, F2_THREADS, smem, st>>>(d, tiles, n_tiles, (const uint16_t*)planes, cmean,
+                                                          cscale, mode, yout, chi_part, spin, status);
+}
 
 void launch_fwd_tc(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
                    const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,
                    int grid, uint64_t spin, int* status, cudaStream_t st) {
     if (n_tiles <= 0) return;
-    const int smem = fwd_tc_smem_bytes(d.N);
     if (grid > n_tiles) grid = n_tiles;
+    const bool s3 = d.fwd_stages == 3;
     if (f16) {
-        cudaFuncSetAttribute(k_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_fwd_tc<true><<<grid, F2_THREADS, smem, st>>>(d, tiles, n_tiles, (const uint16_t*)planes, cmean,
-                                                       cscale, mode, yout, chi_part, spin, status);
+        if (s3) launch_fwd_variant<true, 3>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, grid, spin, status, st);
+        else launch_fwd_variant<true, 4>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, grid, spin, status, st);
     } else {
-        cudaFuncSetAttribute(k_fwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_fwd_tc<false><<<grid, F2_THREADS, smem, st>>>(d, tiles, n_tiles, (const uint16_t*)planes, cmean,
-                                                        cscale, mode, yout, chi_part, spin, status);
+        if (s3) launch_fwd_variant<false, 3>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, grid, spin, status, st);
+        else launch_fwd_variant<false, 4>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, grid, spin, status, st);
     }
 }
 

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
             ((double*)bout)[(int64_t)c * NN + p] = b;
         } else {
             int n = (int)(p / N), m = (int)(p % N);
-            int BN = tc_bn(N);
+            int BN = d.fwd_bn;
             const double cb = b - (cmean ? (double)cmean[(int64_t)c * N + m] : 0.0);
             const int64_t q = tc_plane_index(n, m, N, BN);
             if (fmt == BF_BF16X3) {

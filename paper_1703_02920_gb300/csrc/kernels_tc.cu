@@ -41,14 +41,14 @@ __device__ __forceinline__ cf2 cis_neg(uint64_t p) {
 // core-matrix row), the layout the per-visibility phase recurrences produce.
 // Roles: warps 0-3 drain, warp 4 MMA + TMEM owner, warps 6-13 producers.
 // ===========================================================================
-constexpr int ADJ_STAGES = 3;
+constexpr int ADJ_MAX_STAGES = 3;
 constexpr int ADJ_THREADS = 448;
 
 __host__ __device__ inline int adj_rows(int BLK) { return BLK < 128 ? 128 : BLK; }
 __host__ __device__ inline int adj_stage_bytes(int BLK) {
     return 4 * adj_rows(BLK) * TCA_BK * 2 + 4 * BLK * TCA_BK * 2;
 }
-int adj_tc_smem_bytes(int N) { return ADJ_STAGES * adj_stage_bytes(tca_blk(N)) + 1024; }
+int adj_tc_smem_bytes(int N, int stages) { return stages * adj_stage_bytes(tca_blk(N)) + 1024; }
 __host__ __device__ inline uint32_t adj_tmem_cols(int BLK) {
     int c = (adj_rows(BLK) / 128) * BLK;
     uint32_t p = 32;
@@ -57,8 +57,8 @@ __host__ __device__ inline uint32_t adj_tmem_cols(int BLK) {
 }
 
 struct AdjShared {
-    uint64_t full[ADJ_STAGES];
-    uint64_t empty[ADJ_STAGES];
+    uint64_t full[ADJ_MAX_STAGES];
+    uint64_t empty[ADJ_MAX_STAGES];
     uint64_t tfull;
     uint64_t tempty;
     uint64_t drain;
@@ -70,7 +70,8 @@ struct AdjShared {
 // read from the prepared arrays.
 // F16: FP16X3 operands with y scaled by yscale[0] (a power of two, undone
 // when the partials are summed); otherwise BF16X3.
-template <bool FROM_UV, bool F16>
+// ADJ_STAGES: depth of the shared-memory pipeline (autotuned).
+template <bool FROM_UV, bool F16, int ADJ_STAGES>
 __global__ void __launch_bounds__(ADJ_THREADS, 1)
     k_adj_tc(DevData d, const AdjUnit* __restrict__ units, const int* __restrict__ cta_unit_off,
              const float2* __restrict__ y, const float* __restrict__ yscale, float* __restrict__ partial,
@@ -316,29 +317,35 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
     }
 }
 
+template <bool FROM_UV, bool F16, int STAGES>
+static void launch_adj_variant(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
+                               const float2* y, const float* yscale, float* partial, uint64_t spin,
+                               int* status, cudaStream_t st) {
+    const int smem = adj_tc_smem_bytes(d.N, STAGES);
+    cudaFuncSetAttribute(k_adj_tc<FROM_UV, F16, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_adj_tc<FROM_UV, F16, STAGES><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, yscale,
+                                                                      partial, spin, status);
+}
+
 void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
                    const float2* y, const float* yscale, float* partial, uint64_t spin, int* status,
                    cudaStream_t st) {
     if (n_ctas <= 0) return;
-    int smem = adj_tc_smem_bytes(d.N);
+    const bool s2 = d.adj_stages == 2;
     if (f16) {
-        cudaFuncSetAttribute(k_adj_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_adj_tc<false, true><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, yscale, partial,
-                                                                 spin, status);
+        if (s2) launch_adj_variant<false, true, 2>(d, units, cta_unit_off, n_ctas, y, yscale, partial, spin, status, st);
+        else launch_adj_variant<false, true, 3>(d, units, cta_unit_off, n_ctas, y, yscale, partial, spin, status, st);
     } else {
-        cudaFuncSetAttribute(k_adj_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_adj_tc<false, false><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, yscale, partial,
-                                                                  spin, status);
+        if (s2) launch_adj_variant<false, false, 2>(d, units, cta_unit_off, n_ctas, y, yscale, partial, spin, status, st);
+        else launch_adj_variant<false, false, 3>(d, units, cta_unit_off, n_ctas, y, yscale, partial, spin, status, st);
     }
 }
 
 void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
                       const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st) {
     if (n_ctas <= 0) return;
-    int smem = adj_tc_smem_bytes(d.N);
-    cudaFuncSetAttribute(k_adj_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_adj_tc<true, false><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, nullptr, partial, spin,
-                                                             status);
+    launch_adj_variant<true, false, ADJ_MAX_STAGES>(d, units, cta_unit_off, n_ctas, y, nullptr, partial, spin,
+                                                    status, st);
 }
 
 // Single channel: out[p] = A[p] * (unit partials summed in unit order, FP64).

@@ -54,7 +54,8 @@ _LIB = None
 EXPORTS = ["mem_create", "mem_destroy", "mem_last_error", "mem_status_string", "mem_set_precision",
            "mem_num_vis", "mem_num_images", "mem_forward", "mem_adjoint", "mem_objective_grad",
            "mem_objective_grad_host", "mem_scalars_dev", "mem_solve", "mem_sync", "mem_launch_count",
-           "mem_profile", "mem_profile_read", "mem_adjoint_noalloc", "mem_use_graphs"]
+           "mem_profile", "mem_profile_read", "mem_adjoint_noalloc", "mem_use_graphs", "mem_autotune",
+           "mem_set_tiling", "mem_tiling"]
 
 
 def library_path() -> str:
@@ -108,6 +109,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.mem_profile.restype = ctypes.c_int
     lib.mem_profile_read.argtypes = [P, I32, ctypes.c_char_p, DP, ctypes.POINTER(ctypes.c_int64)]
     lib.mem_profile_read.restype = I32
+    lib.mem_autotune.argtypes = [P, P, I32, ctypes.POINTER(ctypes.c_int32)]
+    lib.mem_autotune.restype = ctypes.c_int
+    lib.mem_set_tiling.argtypes = [P, I32, I32, I32]
+    lib.mem_set_tiling.restype = ctypes.c_int
+    lib.mem_tiling.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.mem_tiling.restype = ctypes.c_int
     lib.mem_use_graphs.argtypes = [P, I32]
     lib.mem_use_graphs.restype = ctypes.c_int
     lib.mem_adjoint_noalloc.argtypes = [I32, D, D, I64, P, P, P, P, P, V]
@@ -212,6 +219,23 @@ def mem_adjoint_noalloc(n, dx, dy, u_dev, v_dev, y_dev, pb_dev, img_dev, stream=
     st = ctypes.c_void_p(0 if stream is None else int(stream))
     _check(load().mem_adjoint_noalloc(int(n), float(dx), float(dy), nv, _ptr(u_dev), _ptr(v_dev),
                                       _ptr(y_dev), _ptr(pb_dev), _ptr(img_dev), st))
+
+
+def mem_autotune(ctx, image_dev, reps: int = 3):
+    """Pick the tensor-core tiling on this context's data; returns (BN, fwd stages, adj stages)."""
+    out = (ctypes.c_int32 * 3)()
+    _check(load().mem_autotune(ctx, _ptr(image_dev), int(reps), out), ctx)
+    return tuple(out)
+
+
+def mem_set_tiling(ctx, fwd_cols: int, fwd_stages: int, adj_stages: int):
+    _check(load().mem_set_tiling(ctx, int(fwd_cols), int(fwd_stages), int(adj_stages)), ctx)
+
+
+def mem_tiling(ctx):
+    out = (ctypes.c_int32 * 3)()
+    _check(load().mem_tiling(ctx, out), ctx)
+    return tuple(out)
 
 
 def mem_use_graphs(ctx, enable: bool):
@@ -322,6 +346,15 @@ class Context:
 
     def launches(self) -> int:
         return mem_launch_count(self.handle)
+
+    def autotune(self, image, reps: int = 3):
+        return mem_autotune(self.handle, self._img(image), reps)
+
+    def set_tiling(self, fwd_cols: int, fwd_stages: int, adj_stages: int):
+        mem_set_tiling(self.handle, fwd_cols, fwd_stages, adj_stages)
+
+    def tiling(self):
+        return mem_tiling(self.handle)
 
     def profile(self, enable: bool = True):
         mem_profile(self.handle, enable)

@@ -21,6 +21,7 @@ pytestmark = pytest.mark.gpu
 TOL_V = {"fp64_direct": 2e-7, "fp32_direct": 1e-5, "bf16x3": 1e-5, "fp16x3": 1e-5}
 TOL_G = {"fp64_direct": 2e-7, "fp32_direct": 1e-4, "bf16x3": 1e-4, "fp16x3": 1e-4}
 TOL_PHI = {"fp64_direct": 1e-11, "fp32_direct": 1e-6, "bf16x3": 1e-6, "fp16x3": 1e-6}
+TOL_CHI = TOL_PHI
 FORMS = ["fp64_direct", "fp32_direct", "bf16x3", "fp16x3"]
 
 
@@ -149,4 +150,65 @@ def test_deterministic_repeat(ms):
     a = ctx.objective_grad(img)
     b = ctx.objective_grad(img)
     assert a[:3] == b[:3] and torch.equal(a[3], b[3])
+    ctx.close()
+
+
+# every tiling the autotuner can choose (and a narrower column block) against
+# the oracle, on images that take one and two column blocks
+TILINGS = [(256, 4, 3), (128, 4, 3), (256, 3, 2), (128, 3, 2), (64, 4, 3)]
+
+
+@pytest.mark.parametrize("form", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("tiling", TILINGS)
+def test_tiling_variants_parity(ms, oracle_mod, form, tiling):
+    import torch
+    ds = S.random_problem(256, 1500, 61, lam=3.0)
+    ctx = ms.Context(ds, precision=form)
+    ctx.set_tiling(*tiling)
+    assert ctx.tiling() == tiling
+    img = ds.truth
+    V = ctx.forward(torch.from_numpy(img).cuda()).cpu().numpy().astype(np.float64)
+    got = V[:, 0] + 1j * V[:, 1]
+    assert _rel_max(got, _oracle_vis(oracle_mod, ds, img)) <= TOL_V[form]
+    phi, chi, Sv, g = ctx.objective_grad(torch.from_numpy(img).cuda())
+    P = oracle_mod.Problem.from_dataset(ds)
+    rphi, rchi, rS, rg = oracle_mod.objective_grad(P, img.astype(np.float64))
+    assert _rel_l2(g.cpu().numpy().astype(np.float64), rg) <= TOL_G[form]
+    assert abs(chi - rchi) <= TOL_CHI[form] * abs(rchi)
+    ctx.close()
+
+
+def test_tiling_rejects_bad_shapes(ms):
+    ds = S.random_problem(128, 100, 62)
+    ctx = ms.Context(ds, precision="fp16x3")
+    for bad in [(256, 4, 3), (48, 4, 3), (128, 5, 3), (128, 4, 4), (96, 4, 3)]:
+        with pytest.raises(ms.MemError):
+            ctx.set_tiling(*bad)
+    ctx.set_tiling(64, 3, 2)
+    assert ctx.tiling() == (64, 3, 2)
+    ctx.close()
+    ctx = ms.Context(ds, precision="fp32_direct")
+    with pytest.raises(ms.MemError):
+        ctx.set_tiling(128, 4, 3)
+    ctx.close()
+
+
+def test_autotune_choice_and_cache(ms, oracle_mod, tmp_path, monkeypatch):
+    import torch
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("MEMSYNTH_TUNE_CACHE", str(cache))
+    ds = S.random_problem(256, 4000, 63, lam=3.0)
+    ctx = ms.Context(ds, precision="fp16x3")
+    img = torch.from_numpy(ds.truth).cuda()
+    choice = ctx.autotune(img, reps=2)
+    assert choice in [(bn, fs, a) for bn in (128, 256) for fs in (3, 4) for a in (2, 3)]
+    assert ctx.tiling() == choice
+    V = ctx.forward(img).cpu().numpy().astype(np.float64)
+    assert _rel_max(V[:, 0] + 1j * V[:, 1], _oracle_vis(oracle_mod, ds, ds.truth)) <= TOL_V["fp16x3"]
+    ctx.close()
+    text = cache.read_text()
+    assert "N=256" in text and text.strip().endswith(" ".join(map(str, choice)))
+    # a new context for the same shape and form starts from the cached choice
+    ctx = ms.Context(ds, precision="fp16x3")
+    assert ctx.tiling() == choice
     ctx.close()
