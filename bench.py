@@ -209,8 +209,8 @@ def main():
 
     tiles = None
     if args.precision in ("bf16x3", "fp16x3"):
-        bn, fs, ast = ctx.autotune(img)
-        tiles = {"fwd_cols": bn, "fwd_stages": fs, "adj_stages": ast}
+        kern, bn, fs, ast = ctx.autotune(img)
+        tiles = {"fwd_kernel": kern, "fwd_cols": bn, "fwd_stages": fs, "adj_stages": ast}
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -275,11 +275,12 @@ def main():
     flops = 4.0 * units
     if name.startswith(("fwd", "adj")) and not name.endswith("reduce"):
         achieved = flops / (avg_ms * 1e-3) / 1e12
-        if name.endswith("tc"):  # both split forms run kind::f16 MMAs at the bf16 rate
+        if name in ("fwd_tc", "fwd_rs", "adj_tc"):  # both split forms run kind::f16 MMAs at the bf16 rate
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "note": f"{name}: {avg_ms:.3f} ms/launch, 4 algorithmic flops per vis*pixel "
+                    "note": f"{name}{' (+ slice combination)' if name == 'fwd_rs' else ''}: "
+                            f"{avg_ms:.3f} ms/launch, 4 algorithmic flops per vis*pixel "
                             f"(12 executed in the 3-term split: executed {3 * achieved:.0f} TFLOP/s); "
                             f"peak = {src} sustained bf16 (fp16 dense rate is the same)"}
         else:

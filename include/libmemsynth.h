@@ -169,25 +169,48 @@ mem_status mem_solve(mem_ctx *ctx, float *image_dev_inout, int32_t n_iter,
  * reported a bounded-wait timeout or a CUDA error occurred. */
 mem_status mem_sync(mem_ctx *ctx);
 
-/* Autotune the tensor-core tiling on this context's data (a no-op for the
- * direct forms): forward image column block (128 or 256 columns when N >=
- * 256) and pipeline depth (3 or 4 stages), adjoint pipeline depth (2 or 3);
- * each candidate is timed over `reps` (0: 3) objective + gradient
- * evaluations at image_dev with per-kernel CUDA events.  The choice is kept
+/* Tensor-core tiling.  fwd_kernel selects the forward kernel:
+ *   MEM_FWD_STREAM    the split image operand streams through shared memory
+ *                     for every 64-visibility tile, in column blocks of
+ *                     fwd_cols (a multiple of 32 dividing N, at most 256);
+ *                     fwd_stages 3 or 4;
+ *   MEM_FWD_RESIDENT  (N <= 256) each CTA keeps a 128-row slice of the split
+ *                     image operand in shared memory and only the phase
+ *                     tables stream; fwd_cols is N; fwd_stages 4 to 6 (as
+ *                     shared memory allows).
+ * adj_stages: adjoint pipeline depth, 2 or 3.  The two forward kernels round
+ * differently (the resident one sums 128-row slices in FP64 and issues the
+ * small correction products before the main ones); both meet the form's
+ * tolerances. */
+typedef enum { MEM_FWD_STREAM = 0, MEM_FWD_RESIDENT = 1 } mem_fwd_kernel;
+
+typedef struct {
+    int32_t fwd_kernel;
+    int32_t fwd_cols;
+    int32_t fwd_stages;
+    int32_t adj_stages;
+} mem_tiling_t;
+
+/* Autotune the tiling on this context's data (a no-op for the direct forms):
+ * every valid (forward kernel, column block, stages) candidate, then the
+ * adjoint depth, each timed over `reps` (0: 3) objective + gradient
+ * evaluations at image_dev with per-kernel CUDA events.  The fastest is kept
  * in the context and appended to a cache file (MEMSYNTH_TUNE_CACHE, default
  * $HOME/.cache/libmemsynth_tune.txt) that mem_create reads back for the same
- * device, N, visibility-count octave, channel count and form.  choice_out
- * (nullable, host): 3 ints (column block, forward stages, adjoint stages). */
-mem_status mem_autotune(mem_ctx *ctx, const float *image_dev, int32_t reps, int32_t *choice_out);
+ * device, N, visibility-count octave, channel count and form.  choice_out:
+ * nullable, host. */
+mem_status mem_autotune(mem_ctx *ctx, const float *image_dev, int32_t reps, mem_tiling_t *choice_out);
 
-/* Set the tensor-core tiling explicitly: the column block a multiple of 32
- * that divides N (at most 256), forward stages 3 or 4, adjoint stages 2 or 3.  Waits for the context's stream.  MEM_EINVAL
- * for a direct form or an invalid shape. */
-mem_status mem_set_tiling(mem_ctx *ctx, int32_t fwd_cols, int32_t fwd_stages, int32_t adj_stages);
+/* Set the tiling explicitly (ranges above; fwd_cols is ignored for
+ * MEM_FWD_RESIDENT).  Waits for the context's stream.  MEM_EINVAL for a
+ * direct form or an invalid choice. */
+mem_status mem_set_tiling(mem_ctx *ctx, const mem_tiling_t *tiling);
 
-/* The tiling in use (3 ints, host): column block, forward stages, adjoint
- * stages.  The direct forms report the defaults, which they do not use. */
-mem_status mem_tiling(const mem_ctx *ctx, int32_t *out3);
+/* The tiling in use.  The direct forms report the defaults, which they do
+ * not use.  Defaults: MEM_FWD_RESIDENT with the deepest pipeline that fits
+ * for N <= 256, else MEM_FWD_STREAM with 256 columns and 4 stages; adjoint
+ * 3 stages. */
+mem_status mem_tiling(const mem_ctx *ctx, mem_tiling_t *out);
 
 /* CUDA graphs (default on): every repeated launch sequence (objective +
  * gradient for given image / gradient pointers, and the solver's evaluation,

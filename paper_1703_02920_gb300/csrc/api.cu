@@ -302,8 +302,11 @@ struct mem_ctx {
     cudaStream_t cap_st = nullptr;
     GraphSlot g_objgrad, g_solve_objgrad, g_solve_curv, g_solve_probe;
 
-    // tensor-core tiling (autotuned)
-    int fwd_bn = 0, fwd_stages = 4, adj_stages = 3;
+    // tensor-core tiling (autotuned): forward kernel (MEM_FWD_STREAM: image
+    // operand streamed per tile, column block fwd_bn; MEM_FWD_RESIDENT: image
+    // slice resident in shared memory, N <= 256), pipeline depths
+    int fwd_kernel = MEM_FWD_STREAM, fwd_bn = 0, fwd_stages = 4, adj_stages = 3;
+    double2* vpart = nullptr;  // resident kernel: slice partials [slice][Z]
     std::string gpu_name;
 
     // optional per-kernel timing (CUDA events on the context stream)
@@ -339,7 +342,7 @@ struct mem_ctx {
         d.off = doff;
         d.dx = dx;
         d.dy = dy;
-        d.fwd_bn = fwd_bn;
+        d.fwd_bn = fwd_kernel == MEM_FWD_RESIDENT ? N : fwd_bn;
         d.fwd_stages = fwd_stages;
         d.adj_stages = adj_stages;
         return d;
@@ -540,6 +543,8 @@ mem_status ensure_buffers(mem_ctx* c) {
         TRY(dalloc(c, &c->ymax_part, (size_t)256));
         const int BLK = tca_blk(c->N);
         TRY(dalloc(c, &c->partial, std::max<size_t>(c->units_h.size(), 1) * BLK * BLK));
+        if (c->N <= 256)
+            TRY(dalloc(c, &c->vpart, (size_t)(c->N / fwd_rs_ks(c->N)) * std::max<int64_t>(c->Z, 1)));
     }
     int ks = 1;
     if (!is_tc(c->prec)) ks = adj_direct_splits(c->dd(), c->num_sms);
@@ -580,7 +585,12 @@ mem_status run_forward(mem_ctx* c, const ImgSrc& src, int mode, bool entropy, vo
     }
     c->launches++;
     TRY(after_launch(c, "prep kernel"));
-    if (tc) {
+    if (tc && c->fwd_kernel == MEM_FWD_RESIDENT) {
+        KTimer t(c, "fwd_rs");
+        launch_fwd_rs(d, f16, c->tiles_tc, c->n_tiles_tc, c->planes, c->cmean, c->cscale, mode, (float2*)yout,
+                      c->chi_part, c->vpart, c->Z, c->num_sms, c->spin, c->dstatus, c->st);
+        if (c->n_tiles_tc > 0) c->launches++;  // + the slice combination
+    } else if (tc) {
         KTimer t(c, "fwd_tc");
         launch_fwd_tc(d, f16, c->tiles_tc, c->n_tiles_tc, c->planes, c->cmean, c->cscale, mode, (float2*)yout,
                       c->chi_part, c->num_sms, c->spin, c->dstatus, c->st);
@@ -753,11 +763,48 @@ std::string tune_path() {
     return std::string(h ? h : ".") + "/.cache/libmemsynth_tune.txt";
 }
 
-bool tune_valid(const mem_ctx* c, int bn, int fs, int as) {
+bool tune_valid(const mem_ctx* c, const mem_tiling_t& t) {
+    if (!(t.adj_stages == 2 || t.adj_stages == 3) || adj_tc_smem_bytes(c->N, t.adj_stages) > 227 * 1024)
+        return false;
+    if (t.fwd_kernel == MEM_FWD_RESIDENT)
+        return c->N <= 256 && t.fwd_stages >= 4 && t.fwd_stages <= fwd_rs_max_stages(c->N);
+    if (t.fwd_kernel != MEM_FWD_STREAM) return false;
     // the epilogue reduces 32-column pairs of 16-column chunks
+    const int bn = t.fwd_cols;
     if (bn < 32 || bn > 256 || c->N % bn != 0 || bn % 32 != 0) return false;
-    if (!(fs == 3 || fs == 4) || !(as == 2 || as == 3)) return false;
-    return fwd_tc_smem_bytes(bn, fs) <= 227 * 1024 && adj_tc_smem_bytes(c->N, as) <= 227 * 1024;
+    if (!(t.fwd_stages == 3 || t.fwd_stages == 4)) return false;
+    return fwd_tc_smem_bytes(bn, t.fwd_stages) <= 227 * 1024;
+}
+
+mem_tiling_t tiling_of(const mem_ctx* c) {
+    mem_tiling_t t;
+    t.fwd_kernel = c->fwd_kernel;
+    t.fwd_cols = c->fwd_kernel == MEM_FWD_RESIDENT ? c->N : c->fwd_bn;
+    t.fwd_stages = c->fwd_stages;
+    t.adj_stages = c->adj_stages;
+    return t;
+}
+
+void apply_tiling(mem_ctx* c, const mem_tiling_t& t) {
+    c->fwd_kernel = t.fwd_kernel;
+    c->fwd_bn = t.fwd_kernel == MEM_FWD_RESIDENT ? c->N : t.fwd_cols;
+    c->fwd_stages = t.fwd_stages;
+    c->adj_stages = t.adj_stages;
+}
+
+void default_tiling(mem_ctx* c) {
+    mem_tiling_t t;
+    if (c->N <= 256) {
+        t.fwd_kernel = MEM_FWD_RESIDENT;
+        t.fwd_cols = c->N;
+        t.fwd_stages = fwd_rs_max_stages(c->N);
+    } else {
+        t.fwd_kernel = MEM_FWD_STREAM;
+        t.fwd_cols = tc_bn(c->N);
+        t.fwd_stages = 4;
+    }
+    t.adj_stages = 3;
+    apply_tiling(c, t);
 }
 
 void tune_load(mem_ctx* c) {
@@ -765,13 +812,9 @@ void tune_load(mem_ctx* c) {
     if (!f) return;
     const std::string key = tune_key(c);
     char k[256];
-    int bn, fs, as;
-    while (std::fscanf(f, "%255s %d %d %d", k, &bn, &fs, &as) == 4)
-        if (key == k && tune_valid(c, bn, fs, as)) {
-            c->fwd_bn = bn;
-            c->fwd_stages = fs;
-            c->adj_stages = as;
-        }
+    mem_tiling_t t;
+    while (std::fscanf(f, "%255s %d %d %d %d", k, &t.fwd_kernel, &t.fwd_cols, &t.fwd_stages, &t.adj_stages) == 5)
+        if (key == k && tune_valid(c, t)) apply_tiling(c, t);
     std::fclose(f);
 }
 
@@ -780,16 +823,13 @@ void tune_store(const mem_ctx* c) {
     const size_t slash = path.rfind('/');
     if (slash != std::string::npos) {
         const std::string dir = path.substr(0, slash);
-        std::string cmd;  // create the directory without a shell
-        for (size_t i = 1; i <= dir.size(); ++i)
-            if (i == dir.size() || dir[i] == '/') {
-                std::string sub = dir.substr(0, i);
-                mkdir(sub.c_str(), 0755);
-            }
+        for (size_t i = 1; i <= dir.size(); ++i)  // create the directory without a shell
+            if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
     }
     FILE* f = std::fopen(path.c_str(), "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %d\n", tune_key(c).c_str(), c->fwd_bn, c->fwd_stages, c->adj_stages);
+    const mem_tiling_t t = tiling_of(c);
+    std::fprintf(f, "%s %d %d %d %d\n", tune_key(c).c_str(), t.fwd_kernel, t.fwd_cols, t.fwd_stages, t.adj_stages);
     std::fclose(f);
 }
 
@@ -853,89 +893,99 @@ int32_t mem_profile_read(mem_ctx* c, int32_t max_kernels, char* names, double* m
     return i;
 }
 
-mem_status mem_autotune(mem_ctx* c, const float* image_dev, int32_t reps, int32_t* choice_out) {
+mem_status mem_autotune(mem_ctx* c, const float* image_dev, int32_t reps, mem_tiling_t* choice_out) {
     if (!c || !image_dev) return fail(c, MEM_EINVAL, "null argument");
-    if (!is_tc(c->prec)) return MEM_OK;  // nothing to tune for the direct forms
+    if (!is_tc(c->prec)) {
+        if (choice_out) *choice_out = tiling_of(c);
+        return MEM_OK;  // nothing to tune for the direct forms
+    }
     if (reps <= 0) reps = 3;
     TRY(ensure_buffers(c));
     const bool prof0 = c->profiling;
     c->profiling = true;
-    auto time_kernel = [&](const char* name, double* best) -> mem_status {
+    // mean per-launch time of the named kernels over `reps` evaluations
+    auto time_kernels = [&](std::initializer_list<const char*> names, double* best) -> mem_status {
         ImgSrc src{image_dev, nullptr, nullptr, nullptr, c->G, 0};
         TRY(run_objgrad(c, src, 0, nullptr, nullptr, nullptr));  // warm-up
         mem_profile_read(c, 0, nullptr, nullptr, nullptr);
         for (int r = 0; r < reps; ++r) TRY(run_objgrad(c, src, 0, nullptr, nullptr, nullptr));
-        char names[32 * 32];
+        char nm[32 * 32];
         double ms[32];
         int64_t cnt[32];
-        const int n = mem_profile_read(c, 32, names, ms, cnt);
-        *best = 1e300;
+        const int n = mem_profile_read(c, 32, nm, ms, cnt);
+        double tot = 0.0;
+        bool seen = false;
         for (int i = 0; i < n; ++i)
-            if (std::strcmp(names + 32 * i, name) == 0) *best = ms[i] / (double)cnt[i];
+            for (const char* want : names)
+                if (std::strcmp(nm + 32 * i, want) == 0) {
+                    tot += ms[i] / (double)reps;
+                    seen = true;
+                }
+        *best = seen ? tot : 1e300;
         return check_status(c);
     };
-    std::vector<int> bns;
-    if (c->N >= 256) bns = {256, 128};
-    else bns = {c->N};
-    int best_bn = c->fwd_bn, best_fs = c->fwd_stages, best_as = c->adj_stages;
+    std::vector<mem_tiling_t> fwd;
+    for (int k : {MEM_FWD_RESIDENT, MEM_FWD_STREAM})
+        for (int bn : {256, 128, 64})
+            for (int fs : {6, 5, 4, 3}) {
+                mem_tiling_t t{k, k == MEM_FWD_RESIDENT ? c->N : bn, fs, c->adj_stages};
+                if (k == MEM_FWD_RESIDENT && bn != 256) continue;  // one column choice
+                if (k == MEM_FWD_STREAM && !(bn == tc_bn(c->N) || (c->N >= 256 && bn == 128))) continue;
+                if (tune_valid(c, t)) fwd.push_back(t);
+            }
+    mem_tiling_t best = tiling_of(c);
     double best_f = 1e300, best_a = 1e300;
     mem_status st = MEM_OK;
-    for (int bn : bns)
-        for (int fs : {4, 3}) {
-            if (!tune_valid(c, bn, fs, c->adj_stages)) continue;
-            c->fwd_bn = bn;
-            c->fwd_stages = fs;
-            double t = 0;
-            if ((st = time_kernel("fwd_tc", &t)) != MEM_OK) break;
-            if (t < best_f) {
-                best_f = t;
-                best_bn = bn;
-                best_fs = fs;
-            }
-        }
-    c->fwd_bn = best_bn;
-    c->fwd_stages = best_fs;
-    for (int as : {3, 2}) {
-        if (st != MEM_OK || !tune_valid(c, c->fwd_bn, c->fwd_stages, as)) continue;
-        c->adj_stages = as;
-        double t = 0;
-        if ((st = time_kernel("adj_tc", &t)) != MEM_OK) break;
-        if (t < best_a) {
-            best_a = t;
-            best_as = as;
+    for (const mem_tiling_t& t : fwd) {
+        apply_tiling(c, t);
+        double ms = 0;
+        // the resident kernel's slice combination is part of its cost
+        if ((st = time_kernels({"fwd_tc", "fwd_rs"}, &ms)) != MEM_OK) break;
+        if (ms < best_f) {
+            best_f = ms;
+            best = t;
         }
     }
-    c->adj_stages = best_as;
+    for (int as : {3, 2}) {
+        mem_tiling_t t = best;
+        t.adj_stages = as;
+        if (st != MEM_OK || !tune_valid(c, t)) continue;
+        apply_tiling(c, t);
+        double ms = 0;
+        if ((st = time_kernels({"adj_tc"}, &ms)) != MEM_OK) break;
+        if (ms < best_a) {
+            best_a = ms;
+            best.adj_stages = as;
+        }
+    }
+    apply_tiling(c, best);
     c->profiling = prof0;
     drop_graphs(c);
     if (st != MEM_OK) return st;
     tune_store(c);
-    if (choice_out) {
-        choice_out[0] = c->fwd_bn;
-        choice_out[1] = c->fwd_stages;
-        choice_out[2] = c->adj_stages;
-    }
+    if (choice_out) *choice_out = best;
     return MEM_OK;
 }
 
-mem_status mem_set_tiling(mem_ctx* c, int32_t fwd_cols, int32_t fwd_stages, int32_t adj_stages) {
-    if (!c) return MEM_EINVAL;
+mem_status mem_set_tiling(mem_ctx* c, const mem_tiling_t* t) {
+    if (!c || !t) return MEM_EINVAL;
     if (!is_tc(c->prec)) return fail(c, MEM_EINVAL, "tiling applies to the tensor-core forms only");
-    if (!tune_valid(c, fwd_cols, fwd_stages, adj_stages))
-        return fail(c, MEM_EINVAL, "tiling: column block must divide N (16..256), stages 3|4 and 2|3");
+    mem_tiling_t x = *t;
+    if (x.fwd_kernel == MEM_FWD_RESIDENT) x.fwd_cols = c->N;
+    if (!tune_valid(c, x))
+        return fail(c, MEM_EINVAL,
+                    "tiling: streaming kernel needs a column block dividing N (32..256, multiple of 32) and 3|4 "
+                    "stages; resident kernel N <= 256 and 4..%d stages; adjoint 2|3 stages",
+                    c->N <= 256 ? fwd_rs_max_stages(c->N) : 0);
     TRY(mem_sync(c));
-    c->fwd_bn = fwd_cols;
-    c->fwd_stages = fwd_stages;
-    c->adj_stages = adj_stages;
+    apply_tiling(c, x);
     drop_graphs(c);
     return MEM_OK;
 }
 
-mem_status mem_tiling(const mem_ctx* c, int32_t* out3) {
-    if (!c || !out3) return MEM_EINVAL;
-    out3[0] = c->fwd_bn;
-    out3[1] = c->fwd_stages;
-    out3[2] = c->adj_stages;
+mem_status mem_tiling(const mem_ctx* c, mem_tiling_t* out) {
+    if (!c || !out) return MEM_EINVAL;
+    *out = tiling_of(c);
     return MEM_OK;
 }
 
@@ -968,6 +1018,8 @@ mem_status mem_set_precision(mem_ctx* c, int32_t prec) {
         return fail(c, MEM_ENOTSUP, "tensor-core forms need N = 64, 128 or a multiple of 256 (N = %d)", c->N);
     c->prec = prec;
     drop_graphs(c);
+    default_tiling(c);
+    if (is_tc(prec)) tune_load(c);
     return ensure_buffers(c);
 }
 
@@ -1030,7 +1082,6 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
                          prop.major, prop.minor));
     c->num_sms = prop.multiProcessorCount;
     c->gpu_name = prop.name;
-    c->fwd_bn = tc_bn(N);
 
     const size_t NN = (size_t)N * N;
     mem_status s;
@@ -1091,6 +1142,7 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
         g_last_error = c->err;
         return bail(MEM_ECUDA);
     }
+    default_tiling(c);
     if (is_tc(c->prec)) tune_load(c);
     if ((s = ensure_buffers(c)) != MEM_OK) {
         g_last_error = c->err;

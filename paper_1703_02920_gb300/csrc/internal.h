@@ -44,8 +44,8 @@ struct DevData {
     const int64_t* off;  // C+1
     double dx, dy;       // pixel size (radians)
     // tensor-core tiling chosen by the autotuner (defaults: tc_bn(N), 4, 3)
-    int fwd_bn;          // forward image column block (divides N, <= 256)
-    int fwd_stages;      // forward pipeline depth (3 or 4)
+    int fwd_bn;          // forward image column block (divides N, <= 256; N for the resident kernel)
+    int fwd_stages;      // forward pipeline depth (streaming 3|4, resident 4..6)
     int adj_stages;      // adjoint pipeline depth (2 or 3)
 };
 
@@ -110,6 +110,16 @@ int adj_direct_splits(const DevData& d, int num_sms);
 
 // Tensor-core forms.
 int fwd_tc_smem_bytes(int BN, int stages);
+// Resident-operand forward (N <= 256): the image rows are cut into slices of
+// fwd_rs_ks(N); each CTA keeps one slice of the operand planes in shared
+// memory; slice partials (FP64, [slice][visibility]) are combined by a second
+// kernel that also applies the forward mode.
+__host__ __device__ inline int fwd_rs_ks(int N) { return N < 128 ? N : 128; }
+int fwd_rs_smem_bytes(int N, int stages);
+int fwd_rs_max_stages(int N);
+void launch_fwd_rs(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
+                   const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,
+                   double2* vpart, int64_t z_total, int num_sms, uint64_t spin, int* status, cudaStream_t st);
 // f16 = 1: FP16X3 operands (planes scaled by cscale[c]); 0: BF16X3.
 void launch_fwd_tc(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
                    const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,

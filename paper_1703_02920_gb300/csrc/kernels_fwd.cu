@@ -283,19 +283,24 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) cq4[slot][k] = __ldg(src + k);
                 };
+                // sum_k Ex[m0+k] t_k = base * sum_{k<8} step_k t_k + base8 * sum_{k<8} step_k t_{k+8}
                 auto reduce_chunk = [&](int q, int slot) {
                     const int m0 = mb * BN + q * 16;
                     const cf2 base = cis_neg(phase_mul(m0 - c0, pa));
                     const cf2 base8 = cmul(base, step8);
                     const float* cq = (const float*)cq4[slot];
-                    float a0 = 0.f, a1 = 0.f;
+                    float ux = 0.f, uy = 0.f, wx = 0.f, wy = 0.f;
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const cf2 ex = cmul(k < 8 ? base : base8, step[k & 7]);
+                    for (int k = 0; k < 8; ++k) {
                         const float tk = fmaf(cq[k], scomp, __uint_as_float(tv[slot][k]));
-                        a0 = fmaf(ex.x, tk, a0);
-                        a1 = fmaf(ex.y, tk, a1);
+                        const float tw = fmaf(cq[k + 8], scomp, __uint_as_float(tv[slot][k + 8]));
+                        ux = fmaf(step[k].x, tk, ux);
+                        uy = fmaf(step[k].y, tk, uy);
+                        wx = fmaf(step[k].x, tw, wx);
+                        wy = fmaf(step[k].y, tw, wy);
                     }
+                    const float a0 = fmaf(base.x, ux, fmaf(-base.y, uy, fmaf(base8.x, wx, -base8.y * wy)));
+                    const float a1 = fmaf(base.x, uy, fmaf(base.y, ux, fmaf(base8.x, wy, base8.y * wx)));
                     two_sum_acc(s0, c0s, a0);
                     two_sum_acc(s1, c1s, a1);
                 };

@@ -44,6 +44,22 @@ class mem_config(ctypes.Structure):
                 ("image_mode", ctypes.c_int32), ("spin_limit", ctypes.c_uint64)]
 
 
+FWD_KERNELS = {"stream": 0, "resident": 1}
+
+
+class mem_tiling_t(ctypes.Structure):
+    _fields_ = [("fwd_kernel", ctypes.c_int32), ("fwd_cols", ctypes.c_int32),
+                ("fwd_stages", ctypes.c_int32), ("adj_stages", ctypes.c_int32)]
+
+    def as_tuple(self):
+        kern = {v: k for k, v in FWD_KERNELS.items()}[self.fwd_kernel]
+        return (kern, self.fwd_cols, self.fwd_stages, self.adj_stages)
+
+
+def _tiling(kernel, cols, fwd_stages, adj_stages):
+    return mem_tiling_t(FWD_KERNELS[kernel], int(cols), int(fwd_stages), int(adj_stages))
+
+
 class mem_solve_report(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("evaluations", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("stopped_early", ctypes.c_int32),
@@ -109,11 +125,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.mem_profile.restype = ctypes.c_int
     lib.mem_profile_read.argtypes = [P, I32, ctypes.c_char_p, DP, ctypes.POINTER(ctypes.c_int64)]
     lib.mem_profile_read.restype = I32
-    lib.mem_autotune.argtypes = [P, P, I32, ctypes.POINTER(ctypes.c_int32)]
+    lib.mem_autotune.argtypes = [P, P, I32, ctypes.POINTER(mem_tiling_t)]
     lib.mem_autotune.restype = ctypes.c_int
-    lib.mem_set_tiling.argtypes = [P, I32, I32, I32]
+    lib.mem_set_tiling.argtypes = [P, ctypes.POINTER(mem_tiling_t)]
     lib.mem_set_tiling.restype = ctypes.c_int
-    lib.mem_tiling.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.mem_tiling.argtypes = [P, ctypes.POINTER(mem_tiling_t)]
     lib.mem_tiling.restype = ctypes.c_int
     lib.mem_use_graphs.argtypes = [P, I32]
     lib.mem_use_graphs.restype = ctypes.c_int
@@ -222,20 +238,22 @@ def mem_adjoint_noalloc(n, dx, dy, u_dev, v_dev, y_dev, pb_dev, img_dev, stream=
 
 
 def mem_autotune(ctx, image_dev, reps: int = 3):
-    """Pick the tensor-core tiling on this context's data; returns (BN, fwd stages, adj stages)."""
-    out = (ctypes.c_int32 * 3)()
-    _check(load().mem_autotune(ctx, _ptr(image_dev), int(reps), out), ctx)
-    return tuple(out)
+    """Pick the tensor-core tiling on this context's data; returns
+    (forward kernel, column block, forward stages, adjoint stages)."""
+    out = mem_tiling_t()
+    _check(load().mem_autotune(ctx, _ptr(image_dev), int(reps), ctypes.byref(out)), ctx)
+    return out.as_tuple()
 
 
-def mem_set_tiling(ctx, fwd_cols: int, fwd_stages: int, adj_stages: int):
-    _check(load().mem_set_tiling(ctx, int(fwd_cols), int(fwd_stages), int(adj_stages)), ctx)
+def mem_set_tiling(ctx, kernel: str, cols: int, fwd_stages: int, adj_stages: int):
+    t = _tiling(kernel, cols, fwd_stages, adj_stages)
+    _check(load().mem_set_tiling(ctx, ctypes.byref(t)), ctx)
 
 
 def mem_tiling(ctx):
-    out = (ctypes.c_int32 * 3)()
-    _check(load().mem_tiling(ctx, out), ctx)
-    return tuple(out)
+    out = mem_tiling_t()
+    _check(load().mem_tiling(ctx, ctypes.byref(out)), ctx)
+    return out.as_tuple()
 
 
 def mem_use_graphs(ctx, enable: bool):
@@ -350,8 +368,8 @@ class Context:
     def autotune(self, image, reps: int = 3):
         return mem_autotune(self.handle, self._img(image), reps)
 
-    def set_tiling(self, fwd_cols: int, fwd_stages: int, adj_stages: int):
-        mem_set_tiling(self.handle, fwd_cols, fwd_stages, adj_stages)
+    def set_tiling(self, kernel: str, cols: int, fwd_stages: int, adj_stages: int):
+        mem_set_tiling(self.handle, kernel, cols, fwd_stages, adj_stages)
 
     def tiling(self):
         return mem_tiling(self.handle)

@@ -154,8 +154,10 @@ def test_deterministic_repeat(ms):
 
 
 # every tiling the autotuner can choose (and a narrower column block) against
-# the oracle, on images that take one and two column blocks
-TILINGS = [(256, 4, 3), (128, 4, 3), (256, 3, 2), (128, 3, 2), (64, 4, 3)]
+# the oracle, on images that take one and two column blocks / row slices
+TILINGS = [("resident", 256, 6, 3), ("resident", 256, 5, 2), ("resident", 256, 4, 3),
+           ("stream", 256, 4, 3), ("stream", 128, 4, 3), ("stream", 256, 3, 2), ("stream", 128, 3, 2),
+           ("stream", 64, 4, 3)]
 
 
 @pytest.mark.parametrize("form", ["bf16x3", "fp16x3"])
@@ -178,18 +180,40 @@ def test_tiling_variants_parity(ms, oracle_mod, form, tiling):
     ctx.close()
 
 
+@pytest.mark.parametrize("N", [64, 128])
+def test_resident_kernel_small_images(ms, oracle_mod, N):
+    """One row slice (N <= 128): forward and chi^2 against the oracle, cube
+    with an empty channel (three channels: a reload of the resident slice at
+    each channel change)."""
+    import torch
+    ds = S.random_problem(N, 0, 64 + N, C=3, z_list=[700, 0, 333], lam=3.0)
+    for form in ["bf16x3", "fp16x3"]:
+        ctx = ms.Context(ds, precision=form)
+        assert ctx.tiling()[0] == "resident"
+        V = ctx.forward(torch.from_numpy(ds.truth).cuda()).cpu().numpy().astype(np.float64)
+        assert _rel_max(V[:, 0] + 1j * V[:, 1], _oracle_vis(oracle_mod, ds, ds.truth)) <= TOL_V[form]
+        ctx.close()
+
+
 def test_tiling_rejects_bad_shapes(ms):
     ds = S.random_problem(128, 100, 62)
     ctx = ms.Context(ds, precision="fp16x3")
-    for bad in [(256, 4, 3), (48, 4, 3), (128, 5, 3), (128, 4, 4), (96, 4, 3)]:
+    for bad in [("stream", 256, 4, 3), ("stream", 48, 4, 3), ("stream", 128, 5, 3), ("stream", 128, 4, 4),
+                ("stream", 96, 4, 3), ("resident", 128, 3, 3), ("resident", 128, 9, 3)]:
         with pytest.raises(ms.MemError):
             ctx.set_tiling(*bad)
-    ctx.set_tiling(64, 3, 2)
-    assert ctx.tiling() == (64, 3, 2)
+    ctx.set_tiling("stream", 64, 3, 2)
+    assert ctx.tiling() == ("stream", 64, 3, 2)
     ctx.close()
     ctx = ms.Context(ds, precision="fp32_direct")
     with pytest.raises(ms.MemError):
-        ctx.set_tiling(128, 4, 3)
+        ctx.set_tiling("stream", 128, 4, 3)
+    ctx.close()
+    big = S.random_problem(512, 50, 65)
+    ctx = ms.Context(big, precision="bf16x3")
+    assert ctx.tiling()[0] == "stream"
+    with pytest.raises(ms.MemError):
+        ctx.set_tiling("resident", 512, 4, 3)
     ctx.close()
 
 
@@ -201,13 +225,17 @@ def test_autotune_choice_and_cache(ms, oracle_mod, tmp_path, monkeypatch):
     ctx = ms.Context(ds, precision="fp16x3")
     img = torch.from_numpy(ds.truth).cuda()
     choice = ctx.autotune(img, reps=2)
-    assert choice in [(bn, fs, a) for bn in (128, 256) for fs in (3, 4) for a in (2, 3)]
+    kern, cols, fs, ast = choice
+    assert (kern == "resident" and cols == 256 and fs in (4, 5, 6)) or \
+        (kern == "stream" and cols in (128, 256) and fs in (3, 4))
+    assert ast in (2, 3)
     assert ctx.tiling() == choice
     V = ctx.forward(img).cpu().numpy().astype(np.float64)
     assert _rel_max(V[:, 0] + 1j * V[:, 1], _oracle_vis(oracle_mod, ds, ds.truth)) <= TOL_V["fp16x3"]
     ctx.close()
     text = cache.read_text()
-    assert "N=256" in text and text.strip().endswith(" ".join(map(str, choice)))
+    code = {"stream": 0, "resident": 1}[kern]
+    assert "N=256" in text and text.strip().endswith(f"{code} {cols} {fs} {ast}")
     # a new context for the same shape and form starts from the cached choice
     ctx = ms.Context(ds, precision="fp16x3")
     assert ctx.tiling() == choice
