@@ -174,6 +174,8 @@ def main():
     ap.add_argument("--precision", default="fp16x3", choices=["bf16x3", "fp16x3", "fp32_direct", "fp64_direct"])
     ap.add_argument("--solve-iters", type=int, default=4)
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="only W + K objective+gradient evaluations with the default tiling (for ncu captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -206,6 +208,15 @@ def main():
 
     def step():
         memsynth.mem_objective_grad(ctx.handle, img, grad, 0, want_scalars=False)
+
+    if args.profile_run:
+        for _ in range(args.warmup + args.steps):
+            step()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": True, "precision": args.precision, "evaluations": args.warmup + args.steps,
+                          "tiling": ctx.tiling(), "launches": ctx.launches()}))
+        ctx.close()
+        return 0
 
     tiles = None
     if args.precision in ("bf16x3", "fp16x3"):
@@ -297,20 +308,25 @@ def main():
     solve = None
     if not args.no_solve and args.solve_iters > 0:
         I0 = torch.full_like(img, float(ds.G))
-        solve = {"iterations": args.solve_iters}
-        for key, prec in (("form", args.precision), ("fp64", "fp64_direct")):
+        solve = {}
+        # the FP64 form takes about a minute per iteration at 256 x 256 and 1e6
+        # visibilities: one timed iteration, no warm-up (its set-up is negligible)
+        for key, prec, iters, warm in (("form", args.precision, args.solve_iters, True),
+                                       ("fp64", "fp64_direct", 1, False)):
             sctx = ctx if prec == args.precision else memsynth.Context(ds, precision=prec)
-            sctx.solve(I0, 1)  # warm-up (graph capture, buffers)
+            if warm:
+                sctx.solve(I0, 1)  # warm-up (graph capture, buffers)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, rep, _ = sctx.solve(I0, args.solve_iters)
+            _, rep, _ = sctx.solve(I0, iters)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
-            solve[key] = {"precision": prec, "s": dt, "ms_per_iter": dt * 1e3 / max(rep.iterations, 1),
+            solve[key] = {"precision": prec, "iterations": rep.iterations, "s": dt,
+                          "ms_per_iter": dt * 1e3 / max(rep.iterations, 1),
                           "evaluations": rep.evaluations, "phi": rep.phi}
             if sctx is not ctx:
                 sctx.close()
-        solve["speedup_vs_fp64"] = solve["fp64"]["s"] / solve["form"]["s"]
+        solve["speedup_vs_fp64_per_iter"] = solve["fp64"]["ms_per_iter"] / solve["form"]["ms_per_iter"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

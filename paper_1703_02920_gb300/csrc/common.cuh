@@ -61,6 +61,17 @@ __device__ __forceinline__ cf2 cmul(cf2 a, cf2 b) {
 // ---------------------------------------------------------------------------
 // Shared-memory addresses, mbarriers
 // ---------------------------------------------------------------------------
+// e^{-2 pi i p / 2^64} from the SFU sine and cosine, rescaled to unit
+// modulus: with x = c^2 + s^2 = 1 + e, the factor 1.5 - x/2 = 1/sqrt(x) + O(e^2)
+// removes a systematic modulus error of the approximations, which would
+// otherwise scale every product of table entries (four per term of Eq. 1).
+__device__ __forceinline__ cf2 cis_neg(uint64_t p) {
+    float s, c;
+    __sincosf(phase_to_angle_f32(p), &s, &c);
+    const float r = fmaf(-0.5f, fmaf(c, c, s * s), 1.5f);
+    return {c * r, -s * r};
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }

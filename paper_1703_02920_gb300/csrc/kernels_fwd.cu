@@ -42,11 +42,6 @@ __host__ __device__ inline uint32_t f2_tmem_cols(int BN) {
     return c;
 }
 
-__device__ __forceinline__ cf2 cis_neg(uint64_t p) {
-    float s, c;
-    __sincosf(phase_to_angle_f32(p), &s, &c);
-    return {c, -s};
-}
 
 struct F2Shared {
     uint64_t full[F2_MAX_STAGES];   // producer warps (8 arrivals)

@@ -42,11 +42,6 @@ constexpr int RS_MAX_STAGES = 6;
 constexpr int RS_APLANE = 128 * TC_BK * 2;  // one A plane of a stage (hi or lo), 8 KB
 constexpr int RS_ABYTES = 2 * RS_APLANE;
 
-__device__ __forceinline__ cf2 cis_neg(uint64_t p) {
-    float s, c;
-    __sincosf(phase_to_angle_f32(p), &s, &c);
-    return {c, -s};
-}
 
 __host__ __device__ inline uint32_t rs_tmem_cols(int N) {
     uint32_t c = 32;

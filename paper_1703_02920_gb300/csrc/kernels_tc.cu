@@ -26,11 +26,6 @@ namespace msk {
 
 // exp(-i 2 pi p) as (cos, -sin), p a fixed-point phase; SFU sincos of an angle
 // reduced exactly to [-pi, pi).
-__device__ __forceinline__ cf2 cis_neg(uint64_t p) {
-    float s, c;
-    __sincosf(phase_to_angle_f32(p), &s, &c);
-    return {c, -s};
-}
 
 // ===========================================================================
 // Adjoint: split-K over visibilities.  A CTA owns a contiguous run of
