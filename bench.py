@@ -174,6 +174,8 @@ def main():
     ap.add_argument("--precision", default="fp16x3", choices=["bf16x3", "fp16x3", "fp32_direct", "fp64_direct"])
     ap.add_argument("--solve-iters", type=int, default=4)
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--tiling", default=None,
+                    help="kernel,cols,fwd_stages,adj_stages (e.g. resident,256,6,3): fixed tiling, no autotuning")
     ap.add_argument("--profile-run", action="store_true",
                     help="only W + K objective+gradient evaluations with the default tiling (for ncu captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -209,6 +211,11 @@ def main():
     def step():
         memsynth.mem_objective_grad(ctx.handle, img, grad, 0, want_scalars=False)
 
+    fixed = None
+    if args.tiling and args.precision in ("bf16x3", "fp16x3"):
+        k, c_, f_, a_ = args.tiling.split(",")
+        fixed = (k, int(c_), int(f_), int(a_))
+        ctx.set_tiling(*fixed)
     if args.profile_run:
         for _ in range(args.warmup + args.steps):
             step()
@@ -220,7 +227,7 @@ def main():
 
     tiles = None
     if args.precision in ("bf16x3", "fp16x3"):
-        kern, bn, fs, ast = ctx.autotune(img)
+        kern, bn, fs, ast = fixed if fixed else ctx.autotune(img)
         tiles = {"fwd_kernel": kern, "fwd_cols": bn, "fwd_stages": fs, "adj_stages": ast}
     for _ in range(args.warmup):
         step()

@@ -34,10 +34,13 @@ namespace msk {
 // FP32 partial buffer; partials are summed in unit order in FP64 afterwards.
 // Operands are MN-major (8 consecutive pixels of one visibility per 16-byte
 // core-matrix row), the layout the per-visibility phase recurrences produce.
-// Roles: warps 0-3 drain, warp 4 MMA + TMEM owner, warps 6-13 producers.
+// Roles: warp 4 MMA + TMEM owner; the other 13 warps produce operand stages,
+// and warps 0-3 (TMEM lane quadrants 0-3) also drain the accumulator to the
+// split-K partials at the end of each unit (once or twice per CTA).
 // ===========================================================================
 constexpr int ADJ_MAX_STAGES = 3;
 constexpr int ADJ_THREADS = 448;
+constexpr int ADJ_PRODUCER_WARPS = ADJ_THREADS / 32 - 1;  // every warp but the MMA warp
 
 __host__ __device__ inline int adj_rows(int BLK) { return BLK < 128 ? 128 : BLK; }
 __host__ __device__ inline int adj_stage_bytes(int BLK) {
@@ -87,7 +90,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < ADJ_STAGES; ++s) {
-            mbar_init(&S.full[s], 8);
+            mbar_init(&S.full[s], ADJ_PRODUCER_WARPS);
             mbar_init(&S.empty[s], 1);
         }
         mbar_init(&S.tfull, 1);
@@ -153,9 +156,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             mbar_wait(&S.drain, 0, 1ull << 32, (volatile int*)&dummy, status);
         }
         __syncwarp();
-    } else if (warp >= 6) {
-        // ------------------------------------------------ producers (256 thr)
-        const int ptid = threadIdx.x - 192;
+    } else {
+        // ------------------------------------------ producers (13 warps, 416 thr)
+        const int ptid = threadIdx.x - (warp > 4 ? 32 : 0);
+        const int n_groups = ADJ_PRODUCER_WARPS * 2;  // 16-thread groups, one item each
         const int jj = ptid & 15;           // visibility within the stage
         const int ngA = R / 8, ngB = BLK / 8;
         const float ysc = F16 ? yscale[0] : 1.f;
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                 sx[6] = cmul(sx[4], sx[2]);
                 sy[7] = cmul(sy[4], sy[3]);
                 sx[7] = cmul(sx[4], sx[3]);
-                for (int item = ptid >> 4; item < ngA + ngB; item += 16) {
+                for (int item = ptid >> 4; item < ngA + ngB; item += n_groups) {
                     uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
                     unsigned char* dst;
                     int plane;
@@ -268,13 +272,9 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.full[s]);
             }
-        }
-    } else if (warp < 4) {
-        // ---------------------------------------------- drain (128 threads)
-        bool ok = true;
-        for (int u = u0; u < u1 && ok; ++u) {
-            const int it = u - u0;
-            ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull, it & 1, spin, abort, status, 1024));
+            if (!ok || warp >= 4) continue;
+            // ------------------------- drain of unit u (warps 0-3, 128 threads)
+            ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull, (u - u0) & 1, spin, abort, status, 1024));
             if (!ok) break;
             tc_fence_after();
             float* out = partial + (int64_t)u * BLK * BLK;
