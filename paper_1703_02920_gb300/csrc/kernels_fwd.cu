@@ -11,8 +11,11 @@
 // and the tensor core's FP32 accumulation (which rounds towards zero) then
 // shrinks T systematically; the centred sums wander around zero instead.
 //
-// A tile is 64 visibilities.  Its A operand has 128 rows: row 2j holds
-// Re Ey[j,:], row 2j+1 holds Im Ey[j,:], so one M=128 MMA produces both the
+// A tile is 64 visibilities.  Its A operand has 128 rows: row
+// 32 (j >> 4) + (j & 15) holds Re Ey[j,:] and the row 16 below it Im Ey[j,:]
+// (an order that keeps the producers' shared-memory stores free of bank
+// conflicts and each visibility's pair of rows in one warp's TMEM lanes), so
+// one M=128 MMA produces both the
 // real and the imaginary part of T for 64 visibilities, and one N <= 256
 // column block covers an N <= 256 image without regenerating Ey.  Two TMEM
 // accumulators (2 x BN columns) let the epilogue of one tile overlap the MMAs
@@ -177,11 +180,13 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
     } else if (warp >= 6) {
         // ----------------------------------- Ey producers (256 threads)
         // thread -> (visibility j = ptid & 63, k-group g = ptid >> 6): 8 image
-        // rows n of one visibility per stage, written as rows 2j (Re), 2j+1 (Im)
+        // rows n of one visibility per stage, written as A rows row(j, Re), row(j, Im)
         const int ptid = threadIdx.x - 192;
         const int jv = ptid & 63, g = ptid >> 6;
-        const int r0 = 2 * jv;
-        const int off = (g * 16 + (r0 >> 3)) * 128 + (r0 & 7) * 16;  // row 2j; row 2j+1 at +16
+        // row(j, c) = 32 (j >> 4) + 16 c + (j & 15): the 32 lanes of a store
+        // instruction fill four whole 128-byte core matrices (no bank conflicts)
+        const int r0 = 32 * (jv >> 4) + (jv & 15);
+        const int off = (g * 16 + (r0 >> 3)) * 128 + (r0 & 7) * 16;  // Re row; Im row at +256
         uint32_t sc = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
@@ -215,9 +220,9 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                         split16x2<F16>(z[6].y, z[7].y, ih.w, il.w);
                     }
                     *(uint4*)(A + off) = rh;
-                    *(uint4*)(A + off + 16) = ih;
+                    *(uint4*)(A + off + 256) = ih;
                     *(uint4*)(A + F2_APLANE + off) = rl;
-                    *(uint4*)(A + F2_APLANE + off + 16) = il;
+                    *(uint4*)(A + F2_APLANE + off + 256) = il;
                     fence_async_smem();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&S.full[s]);
@@ -226,12 +231,12 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
         }
     } else {
         // -------------------------------- epilogue (warps 0-3, 128 threads)
-        // lane r = A row: visibility j = r / 2, component r & 1 (0: Re T, 1: Im T).
-        // Every lane accumulates (sum ReEx T, sum ImEx T) over its row; the
-        // even/odd pair combines with one shuffle:
+        // TMEM lane = A row: warp q holds visibilities 16q .. 16q+15, lane L
+        // component L >> 4 (0: Re T, 1: Im T) of visibility 16q + (L & 15).
+        // Every lane accumulates (sum ReEx T, sum ImEx T) over its row; lanes L
+        // and L ^ 16 combine with one shuffle:
         //   Re V = sum ReEx ReT - ImEx ImT,  Im V = sum ReEx ImT + ImEx ReT.
-        const int row = threadIdx.x;
-        const int jv = row >> 1, comp = row & 1;
+        const int jv = 16 * warp + (lane & 15), comp = lane >> 4;
         uint32_t it = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
@@ -314,11 +319,11 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                 if (lane == 0) mbar_arrive(&S.tempty[b]);
             }
             if (!ok) break;
-            // even lane: (sum ReEx ReT, sum ImEx ReT); odd lane: (sum ReEx ImT, sum ImEx ImT)
+            // lane < 16: (sum ReEx ReT, sum ImEx ReT); lane >= 16: (sum ReEx ImT, sum ImEx ImT)
             const double inv = 1.0 / (double)osc;
             const double p0 = ((double)s0 + (double)c0s) * inv, p1 = ((double)s1 + (double)c1s) * inv;
-            const double q0 = __shfl_xor_sync(0xffffffffu, p0, 1);
-            const double q1 = __shfl_xor_sync(0xffffffffu, p1, 1);
+            const double q0 = __shfl_xor_sync(0xffffffffu, p0, 16);
+            const double q1 = __shfl_xor_sync(0xffffffffu, p1, 16);
             double chi = 0.0;
             if (valid && comp == 0) {
                 const double Vre = p0 - q1;  // ReEx ReT - ImEx ImT

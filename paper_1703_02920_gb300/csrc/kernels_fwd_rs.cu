@@ -23,8 +23,8 @@
 // then act on an accumulator of full magnitude.  This costs a second pass of
 // the phase-table producers (hi plane only) over the slice.
 //
-// Tile: 64 visibilities, A rows 2j (Re Ey) and 2j+1 (Im Ey) as in the
-// streaming kernel.  Roles (416 threads): warps 0-3 epilogue (TMEM lane = A
+// Tile: 64 visibilities, A rows 32 (j >> 4) + (j & 15) (Re Ey) and 16 below
+// (Im Ey), as in the streaming kernel.  Roles (416 threads): warps 0-3 epilogue (TMEM lane = A
 // row), warp 4 MMA issuer, TMEM owner and resident-operand loader, warps 5-12
 // Ey producers.  Every wait is bounded.
 #include <algorithm>
@@ -181,11 +181,13 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     } else if (warp >= 5) {
         // --------------------------------------- Ey producers (256 threads)
         // thread -> (visibility j = ptid & 63, row group g = ptid >> 6): 8 image
-        // rows of one visibility per stage, written as A rows 2j (Re), 2j+1 (Im)
+        // rows of one visibility per stage, written as A rows row(j, Re), row(j, Im)
         const int ptid = threadIdx.x - 160;
         const int jv = ptid & 63, g = ptid >> 6;
-        const int r0 = 2 * jv;
-        const int off = (g * 16 + (r0 >> 3)) * 128 + (r0 & 7) * 16;  // row 2j; row 2j+1 at +16
+        // row(j, c) = 32 (j >> 4) + 16 c + (j & 15): the 32 lanes of a store
+        // instruction fill four whole 128-byte core matrices (no bank conflicts)
+        const int r0 = 32 * (jv >> 4) + (jv & 15);
+        const int off = (g * 16 + (r0 >> 3)) * 128 + (r0 & 7) * 16;  // Re row; Im row at +256
         uint32_t sc = 0;
         bool ok = true;
         for (int t = t_begin; t < t_end && ok; ++t) {
@@ -219,10 +221,10 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                         split16x2<F16>(z[6].y, z[7].y, ih.w, il.w);
                     }
                     *(uint4*)(A + off) = rh;
-                    *(uint4*)(A + off + 16) = ih;
+                    *(uint4*)(A + off + 256) = ih;
                     if (pass == 0) {  // the hi*hi pass reads the hi plane only
                         *(uint4*)(A + RS_APLANE + off) = rl;
-                        *(uint4*)(A + RS_APLANE + off + 16) = il;
+                        *(uint4*)(A + RS_APLANE + off + 256) = il;
                     }
                     fence_async_smem();
                     __syncwarp();
@@ -232,9 +234,9 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
         }
     } else {
         // -------------------------------- epilogue (warps 0-3, 128 threads)
-        // lane r = A row: visibility j = r / 2, component r & 1 (0: Re T, 1: Im T)
-        const int row = threadIdx.x;
-        const int jv = row >> 1, comp = row & 1;
+        // TMEM lane = A row: warp q holds visibilities 16q .. 16q+15, lane L
+        // component L >> 4 (0: Re T, 1: Im T) of visibility 16q + (L & 15)
+        const int jv = 16 * warp + (lane & 15), comp = lane >> 4;
         uint32_t it = 0;
         bool ok = true;
         for (int t = t_begin; t < t_end && ok; ++t, ++it) {
@@ -313,11 +315,11 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.tempty[b]);
-            // even lane: (sum ReEx ReT, sum ImEx ReT); odd lane: (sum ReEx ImT, sum ImEx ImT)
+            // lane < 16: (sum ReEx ReT, sum ImEx ReT); lane >= 16: (sum ReEx ImT, sum ImEx ImT)
             const double inv = 1.0 / (double)osc;
             const double p0 = ((double)s0 + (double)c0s) * inv, p1 = ((double)s1 + (double)c1s) * inv;
-            const double q0 = __shfl_xor_sync(0xffffffffu, p0, 1);
-            const double q1 = __shfl_xor_sync(0xffffffffu, p1, 1);
+            const double q0 = __shfl_xor_sync(0xffffffffu, p0, 16);
+            const double q1 = __shfl_xor_sync(0xffffffffu, p1, 16);
             if (valid && comp == 0) vpart[(int64_t)slice * z_total + j] = make_double2(p0 - q1, q0 + p1);
         }
     }
