@@ -207,9 +207,8 @@ mem_status mem_autotune(mem_ctx *ctx, const float *image_dev, int32_t reps, mem_
 mem_status mem_set_tiling(mem_ctx *ctx, const mem_tiling_t *tiling);
 
 /* The tiling in use.  The direct forms report the defaults, which they do
- * not use.  Defaults: MEM_FWD_RESIDENT with the deepest pipeline that fits
- * for N <= 256, else MEM_FWD_STREAM with 256 columns and 4 stages; adjoint
- * 3 stages. */
+ * not use.  Defaults (before mem_autotune or a cached choice):
+ * MEM_FWD_STREAM with min(N, 256) columns and 4 stages; adjoint 3 stages. */
 mem_status mem_tiling(const mem_ctx *ctx, mem_tiling_t *out);
 
 /* CUDA graphs (default on): every repeated launch sequence (objective +

@@ -794,15 +794,9 @@ void apply_tiling(mem_ctx* c, const mem_tiling_t& t) {
 
 void default_tiling(mem_ctx* c) {
     mem_tiling_t t;
-    if (c->N <= 256) {
-        t.fwd_kernel = MEM_FWD_RESIDENT;
-        t.fwd_cols = c->N;
-        t.fwd_stages = fwd_rs_max_stages(c->N);
-    } else {
-        t.fwd_kernel = MEM_FWD_STREAM;
-        t.fwd_cols = tc_bn(c->N);
-        t.fwd_stages = 4;
-    }
+    t.fwd_kernel = MEM_FWD_STREAM;
+    t.fwd_cols = tc_bn(c->N);
+    t.fwd_stages = 4;
     t.adj_stages = 3;
     apply_tiling(c, t);
 }

@@ -217,6 +217,18 @@ class Dataset:
         a, b = int(self.offsets[c]), int(self.offsets[c + 1])
         return self.u[a:b], self.v[a:b], self.vo[a:b], self.sigma[a:b]
 
+    def subset(self, channels) -> "Dataset":
+        """The data set restricted to the listed channels (in that order)."""
+        channels = list(channels)
+        sl = [slice(int(self.offsets[c]), int(self.offsets[c + 1])) for c in channels]
+        offs = np.concatenate([[0], np.cumsum([s.stop - s.start for s in sl])]).astype(np.int64)
+        cat = lambda a: np.concatenate([a[s] for s in sl])
+        truth = self.truth[:1] if self.shared_image else self.truth[channels]
+        return Dataset(name=f"{self.name}[{channels}]", N=self.N, dx=self.dx, dy=self.dy, u=cat(self.u),
+                       v=cat(self.v), vo=cat(self.vo), sigma=cat(self.sigma), pb=self.pb[channels],
+                       offsets=offs, truth=truth, G=self.G, lam=self.lam, n_iter=self.n_iter,
+                       shared_image=self.shared_image, meta=dict(self.meta))
+
 
 # Section 4 workloads are ALMA data sets; these stand-ins follow their shapes.
 CONFIGS = {
