@@ -773,7 +773,7 @@ bool tune_valid(const mem_ctx* c, const mem_tiling_t& t) {
     const int bn = t.fwd_cols;
     if (bn < 32 || bn > 256 || c->N % bn != 0 || bn % 32 != 0) return false;
     if (!(t.fwd_stages == 3 || t.fwd_stages == 4)) return false;
-    return fwd_tc_smem_bytes(bn, t.fwd_stages) <= 227 * 1024;
+    return fwd_tc_smem_bytes(c->N, bn, t.fwd_stages) <= 227 * 1024;
 }
 
 mem_tiling_t tiling_of(const mem_ctx* c) {

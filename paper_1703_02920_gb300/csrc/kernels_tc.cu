@@ -160,6 +160,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
         // ------------------------------------------ producers (13 warps, 416 thr)
         const int ptid = threadIdx.x - (warp > 4 ? 32 : 0);
         const int n_groups = ADJ_PRODUCER_WARPS * 2;  // 16-thread groups, one item each
+        // half of the groups write Ey items (A operand), half P items (B operand),
+        // so that each thread builds one step table per stage
+        const bool ey_side = (ptid >> 4) < n_groups / 2;
+        const int side_grp = ey_side ? (ptid >> 4) : (ptid >> 4) - n_groups / 2;
         const int jj = ptid & 15;           // visibility within the stage
         const int ngA = R / 8, ngB = BLK / 8;
         const float ysc = F16 ? yscale[0] : 1.f;
@@ -200,25 +204,19 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                 if (!ok) break;
                 unsigned char* A = smem + s * stage_bytes;
                 unsigned char* B = A + 4 * a_plane;
-                // rotation steps exp(-i 2 pi q a), q = 0..7, by powers of one SFU value
-                cf2 sy[8], sx[8];
-                sy[0] = {1.f, 0.f};
-                sx[0] = {1.f, 0.f};
-                sy[1] = cis_neg(pb);
-                sx[1] = cis_neg(pa);
-                sy[2] = cmul(sy[1], sy[1]);
-                sx[2] = cmul(sx[1], sx[1]);
-                sy[4] = cmul(sy[2], sy[2]);
-                sx[4] = cmul(sx[2], sx[2]);
-                sy[3] = cmul(sy[2], sy[1]);
-                sx[3] = cmul(sx[2], sx[1]);
-                sy[5] = cmul(sy[4], sy[1]);
-                sx[5] = cmul(sx[4], sx[1]);
-                sy[6] = cmul(sy[4], sy[2]);
-                sx[6] = cmul(sx[4], sx[2]);
-                sy[7] = cmul(sy[4], sy[3]);
-                sx[7] = cmul(sx[4], sx[3]);
-                for (int item = ptid >> 4; item < ngA + ngB; item += n_groups) {
+                // rotation steps exp(-i 2 pi q c), q = 0..7, by powers of one SFU
+                // value: c = b for the Ey side, a for the P side
+                cf2 st[8];
+                st[0] = {1.f, 0.f};
+                st[1] = cis_neg(ey_side ? pb : pa);
+                st[2] = cmul(st[1], st[1]);
+                st[4] = cmul(st[2], st[2]);
+                st[3] = cmul(st[2], st[1]);
+                st[5] = cmul(st[4], st[1]);
+                st[6] = cmul(st[4], st[2]);
+                st[7] = cmul(st[4], st[3]);
+                for (int it2 = side_grp; it2 < (ey_side ? ngA : ngB); it2 += n_groups / 2) {
+                    const int item = ey_side ? it2 : ngA + it2;
                     uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
                     unsigned char* dst;
                     int plane;
@@ -229,7 +227,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                             const cf2 base = cis_neg(phase_mul(n0 - c0, pb));
                             cf2 z[8];
 #pragma unroll
-                            for (int q = 0; q < 8; ++q) z[q] = cmul(base, sy[q]);
+                            for (int q = 0; q < 8; ++q) z[q] = cmul(base, st[q]);
                             split16x2<F16>(z[0].x, z[1].x, rh.x, rl.x);
                             split16x2<F16>(z[2].x, z[3].x, rh.y, rl.y);
                             split16x2<F16>(z[4].x, z[5].x, rh.z, rl.z);
@@ -250,7 +248,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                             const cf2 base = cmul(yv, cf2{e.x, -e.y});
                             cf2 z[8];
 #pragma unroll
-                            for (int q = 0; q < 8; ++q) z[q] = cmul(base, cf2{sx[q].x, -sx[q].y});
+                            for (int q = 0; q < 8; ++q) z[q] = cmul(base, cf2{st[q].x, -st[q].y});
                             split16x2<F16>(z[0].x, z[1].x, rh.x, rl.x);
                             split16x2<F16>(z[2].x, z[3].x, rh.y, rl.y);
                             split16x2<F16>(z[4].x, z[5].x, rh.z, rl.z);

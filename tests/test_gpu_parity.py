@@ -189,7 +189,7 @@ def test_resident_kernel_small_images(ms, oracle_mod, N):
     ds = S.random_problem(N, 0, 64 + N, C=3, z_list=[700, 0, 333], lam=3.0)
     for form in ["bf16x3", "fp16x3"]:
         ctx = ms.Context(ds, precision=form)
-        assert ctx.tiling()[0] == "resident"
+        ctx.set_tiling("resident", N, 4, 3)
         V = ctx.forward(torch.from_numpy(ds.truth).cuda()).cpu().numpy().astype(np.float64)
         assert _rel_max(V[:, 0] + 1j * V[:, 1], _oracle_vis(oracle_mod, ds, ds.truth)) <= TOL_V[form]
         ctx.close()
