@@ -181,7 +181,8 @@ mem_status mem_sync(mem_ctx *ctx);
  * adj_stages: adjoint pipeline depth, 2 or 3.  The two forward kernels round
  * differently (the resident one sums 128-row slices in FP64 and issues the
  * small correction products before the main ones); both meet the form's
- * tolerances. */
+ * tolerances; at a solve's final image the resident order halves the chi^2
+ * error. */
 typedef enum { MEM_FWD_STREAM = 0, MEM_FWD_RESIDENT = 1 } mem_fwd_kernel;
 
 typedef struct {
@@ -207,8 +208,10 @@ mem_status mem_autotune(mem_ctx *ctx, const float *image_dev, int32_t reps, mem_
 mem_status mem_set_tiling(mem_ctx *ctx, const mem_tiling_t *tiling);
 
 /* The tiling in use.  The direct forms report the defaults, which they do
- * not use.  Defaults (before mem_autotune or a cached choice):
- * MEM_FWD_STREAM with min(N, 256) columns and 4 stages; adjoint 3 stages. */
+ * not use.  Defaults (before mem_autotune or a cached choice): for N <= 128
+ * MEM_FWD_RESIDENT with the deepest pipeline that fits (mem_autotune keeps
+ * the resident kernel there: it is the more accurate one, see above), for
+ * N >= 256 MEM_FWD_STREAM with 256 columns and 4 stages; adjoint 3 stages. */
 mem_status mem_tiling(const mem_ctx *ctx, mem_tiling_t *out);
 
 /* CUDA graphs (default on): every repeated launch sequence (objective +

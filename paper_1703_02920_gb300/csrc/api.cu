@@ -773,7 +773,7 @@ bool tune_valid(const mem_ctx* c, const mem_tiling_t& t) {
     const int bn = t.fwd_cols;
     if (bn < 32 || bn > 256 || c->N % bn != 0 || bn % 32 != 0) return false;
     if (!(t.fwd_stages == 3 || t.fwd_stages == 4)) return false;
-    return fwd_tc_smem_bytes(c->N, bn, t.fwd_stages) <= 227 * 1024;
+    return fwd_tc_smem_bytes(bn, t.fwd_stages) <= 227 * 1024;
 }
 
 mem_tiling_t tiling_of(const mem_ctx* c) {
@@ -792,11 +792,20 @@ void apply_tiling(mem_ctx* c, const mem_tiling_t& t) {
     c->adj_stages = t.adj_stages;
 }
 
+// N <= 128: the resident kernel (one row slice, no duplicated work; its
+// corrections-first order halves the chi^2 error at a solve's final image);
+// N >= 256: the streaming kernel (about 1.7x faster than two resident slices).
 void default_tiling(mem_ctx* c) {
     mem_tiling_t t;
-    t.fwd_kernel = MEM_FWD_STREAM;
-    t.fwd_cols = tc_bn(c->N);
-    t.fwd_stages = 4;
+    if (c->N <= 128) {
+        t.fwd_kernel = MEM_FWD_RESIDENT;
+        t.fwd_cols = c->N;
+        t.fwd_stages = fwd_rs_max_stages(c->N);
+    } else {
+        t.fwd_kernel = MEM_FWD_STREAM;
+        t.fwd_cols = tc_bn(c->N);
+        t.fwd_stages = 4;
+    }
     t.adj_stages = 3;
     apply_tiling(c, t);
 }
@@ -925,6 +934,7 @@ mem_status mem_autotune(mem_ctx* c, const float* image_dev, int32_t reps, mem_ti
                 mem_tiling_t t{k, k == MEM_FWD_RESIDENT ? c->N : bn, fs, c->adj_stages};
                 if (k == MEM_FWD_RESIDENT && bn != 256) continue;  // one column choice
                 if (k == MEM_FWD_STREAM && !(bn == tc_bn(c->N) || (c->N >= 256 && bn == 128))) continue;
+                if (k == MEM_FWD_STREAM && c->N <= 128) continue;  // accuracy: resident only
                 if (tune_valid(c, t)) fwd.push_back(t);
             }
     mem_tiling_t best = tiling_of(c);

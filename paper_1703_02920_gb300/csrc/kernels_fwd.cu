@@ -189,17 +189,10 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
         const int off = (g * 16 + (r0 >> 3)) * 128 + (r0 & 7) * 16;  // Re row; Im row at +256
         uint32_t sc = 0;
         bool ok = true;
-        // the next tile's record and phase are loaded one tile ahead
-        VisTile tl_n = blockIdx.x < n_tiles ? tiles[blockIdx.x] : VisTile{0, 0, 0};
-        uint64_t pb_n = jv < tl_n.count ? d.pb[tl_n.start + jv] : 0;
         for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-            const VisTile tl = tl_n;
+            const VisTile tl = tiles[t];
             const bool valid = jv < tl.count;
-            const uint64_t pb = pb_n;
-            if (t + (int)gridDim.x < n_tiles) {
-                tl_n = tiles[t + gridDim.x];
-                pb_n = jv < tl_n.count ? d.pb[tl_n.start + jv] : 0;
-            }
+            const uint64_t pb = valid ? d.pb[tl.start + jv] : 0;
             cf2 step[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) step[q] = cis_neg(phase_mul(q, pb));
@@ -246,27 +239,11 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
         const int jv = 16 * warp + (lane & 15), comp = lane >> 4;
         uint32_t it = 0;
         bool ok = true;
-        float* cms = (float*)(smem + (size_t)F2_STAGES * stage_bytes) + warp * N;
-        int cm_chan = -1;
-        // the next tile's record and phases are loaded one tile ahead
-        VisTile tl_n = blockIdx.x < n_tiles ? tiles[blockIdx.x] : VisTile{0, 0, 0};
-        uint64_t pa_n = 0, pb_n = 0;
-        if (blockIdx.x < n_tiles) {
-            const int64_t jn = tl_n.start + (jv < tl_n.count ? jv : 0);
-            pa_n = d.pa[jn];
-            pb_n = d.pb[jn];
-        }
         for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-            const VisTile tl = tl_n;
+            const VisTile tl = tiles[t];
             const bool valid = jv < tl.count;
             const int64_t j = tl.start + (valid ? jv : 0);
-            const uint64_t pa = pa_n, pb_cur = pb_n;
-            if (t + (int)gridDim.x < n_tiles) {
-                tl_n = tiles[t + gridDim.x];
-                const int64_t jn = tl_n.start + (jv < tl_n.count ? jv : 0);
-                pa_n = d.pa[jn];
-                pb_n = d.pb[jn];
-            }
+            const uint64_t pa = d.pa[j];
             cf2 step[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) step[q] = cis_neg(phase_mul(q, pa));
@@ -275,7 +252,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             // the exact half-turn and N/2-multiple phases)
             float scomp;
             {
-                const uint64_t pb = pb_cur;
+                const uint64_t pb = d.pb[j];
                 const float th = (float)(int64_t)((int64_t)pb >> 1) * 5.421010862427522e-20f;  // b/2, turns
                 const float tn = (float)(int64_t)phase_mul(N / 2, pb) * 5.421010862427522e-20f;  // N b/2
                 float sh, ch;
@@ -286,13 +263,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             }
             const float osc = F16 ? cscale[tl.chan] : 1.f;  // operand scale (power of two)
             scomp *= osc;
-            if (tl.chan != cm_chan) {
-                // this warp's copy of the channel's column means (read as broadcasts)
-                const float4* src = (const float4*)(cmean + (int64_t)tl.chan * N);
-                for (int i = lane; i < N / 4; i += 32) ((float4*)cms)[i] = __ldg(src + i);
-                __syncwarp();
-                cm_chan = tl.chan;
-            }
+            const float* cm = cmean + (int64_t)tl.chan * N;
             float s0 = 0.f, s1 = 0.f, c0s = 0.f, c1s = 0.f;  // compensated sums
             for (int mb = 0; mb < n_mb; ++mb, ++it) {
                 const int b = it & 1;
@@ -301,19 +272,23 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * BN);
-                // software pipeline over 16-column chunks: the TMEM load of chunk
-                // q+1 is in flight while chunk q is reduced
+                // software pipeline over 16-column chunks: the TMEM load and the
+                // column means of chunk q+1 are in flight while chunk q is reduced
                 const int nq = BN / 16;
                 uint32_t tv[2][16];
-                auto load_chunk = [&](int q, int slot) { tmem_ld16(lane_base + q * 16, tv[slot]); };
+                float4 cq4[2][4];
+                auto load_chunk = [&](int q, int slot) {
+                    tmem_ld16(lane_base + q * 16, tv[slot]);
+                    const float4* src = (const float4*)(cm + mb * BN + q * 16);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) cq4[slot][k] = __ldg(src + k);
+                };
                 // sum_k Ex[m0+k] t_k = base * sum_{k<8} step_k t_k + base8 * sum_{k<8} step_k t_{k+8}
                 auto reduce_chunk = [&](int q, int slot) {
                     const int m0 = mb * BN + q * 16;
                     const cf2 base = cis_neg(phase_mul(m0 - c0, pa));
                     const cf2 base8 = cmul(base, step8);
-                    float cq[16];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) *(float4*)&cq[4 * k] = ((const float4*)(cms + m0))[k];
+                    const float* cq = (const float*)cq4[slot];
                     float ux = 0.f, uy = 0.f, wx = 0.f, wy = 0.f;
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
@@ -388,14 +363,13 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
 
 }  // namespace
 
-// stages, then 4 warps' copies of a channel's column means, then alignment slack
-int fwd_tc_smem_bytes(int N, int BN, int stages) { return stages * f2_stage_bytes(BN) + 16 * N + 1024; }
+int fwd_tc_smem_bytes(int BN, int stages) { return stages * f2_stage_bytes(BN) + 1024; }
 
 template <bool F16, int STAGES>
 static void launch_fwd_variant(const DevData& d, const VisTile* tiles, int n_tiles, const void* planes,
                                const float* cmean, const float* cscale, int mode, float2* yout,
                                double* chi_part, int grid, uint64_t spin, int* status, cudaStream_t st) {
-    const int smem = fwd_tc_smem_bytes(d.N, d.fwd_bn, STAGES);
+    const int smem = fwd_tc_smem_bytes(d.fwd_bn, STAGES);
     cudaFuncSetAttribute(k_fwd_tc<F16, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_fwd_tc<F16, STAGES><<<grid, F2_THREADS, smem, st>>>(d, tiles, n_tiles, (const uint16_t*)planes, cmean,
                                                           cscale, mode, yout, chi_part, spin, status);
