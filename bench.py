@@ -119,6 +119,21 @@ def _traffic(kernel: str):
         return None
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value (replicas: each rank times its own copy)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units: int, world: int, ms_step: float) -> float:
+    """Whole-job throughput: every rank processes `units` per step."""
+    return units * world / (ms_step * 1e-3)
+
+
 def make_data(config: int):
     from paper_1703_02920_gb300 import synth
     return synth.make(config)
@@ -268,12 +283,8 @@ def main():
     launches = ctx.launches() - launches0
     ctx.sync()
     ms = [a.elapsed_time(b) for a, b in ev]
-    ms_step = sum(ms) / len(ms)
-    if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = units * world / (ms_step * 1e-3)
+    ms_step = max_over_ranks(sum(ms) / len(ms), dist, "cuda")
+    value = job_value(units, world, ms_step)
 
     # ---- per-kernel durations: the same steps again with every launch bracketed
     # by CUDA events on the context stream (direct launches, no graph)
@@ -297,7 +308,7 @@ def main():
         t0 = time.perf_counter()
         memsynth.mem_objective_grad_host(ctx.handle, himg, hgrad, 0)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_val = units * world / (statistics.mean(e2e_ms) * 1e-3)
+    e2e_val = job_value(units, world, max_over_ranks(statistics.mean(e2e_ms), dist, "cuda"))
 
     # ---- roofline of the dominant kernel (algorithmic flops per launch / event time)
     peaks, src = _peaks()
