@@ -1,0 +1,75 @@
+"""Error of every result against the FP64 oracle, per precision form,
+printed as a table (pytest -s) and held to the stated bounds:
+  config 1 (64 x 64, 10,260 visibilities, 50 CG iterations from I = G) -
+    model visibilities at the truth, chi^2 and gradient at the truth, final
+    image and final objective of the solve;
+  a 256 x 256 random problem (20,000 visibilities) - visibilities, chi^2,
+    gradient.
+"""
+import numpy as np
+import pytest
+
+from paper_1703_02920_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+FORMS = ["fp64_direct", "fp32_direct", "bf16x3", "fp16x3"]
+
+
+@pytest.fixture(scope="module")
+def ms():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1703_02920_gb300 import memsynth
+    memsynth.load()
+    return memsynth
+
+
+def _errors(ms, oracle_mod, ds, form, img):
+    import torch
+    P = oracle_mod.Problem.from_dataset(ds)
+    ref = np.concatenate(oracle_mod.model_vis(P, img.astype(np.float64)))
+    rphi, rchi, rS, rg = oracle_mod.objective_grad(P, img.astype(np.float64))
+    ctx = ms.Context(ds, precision=form)
+    t = torch.from_numpy(img).cuda()
+    V = ctx.forward(t).cpu().numpy().astype(np.float64)
+    phi, chi, Sv, g = ctx.objective_grad(t)
+    ctx.close()
+    got = V[:, 0] + 1j * V[:, 1]
+    g = g.cpu().numpy().astype(np.float64)
+    return dict(vis=np.max(np.abs(got - ref)) / np.max(np.abs(ref)), chi2=abs(chi - rchi) / abs(rchi),
+                phi=abs(phi - rphi) / abs(rphi), grad=np.linalg.norm(g - rg) / np.linalg.norm(rg))
+
+
+def test_error_table(ms, oracle_mod):
+    import torch
+    rows = []
+    ds1 = S.make(1)
+    P1 = oracle_mod.Problem.from_dataset(ds1)
+    ref_img, hist = oracle_mod.solve(P1, np.full((1, ds1.N, ds1.N), ds1.G), ds1.n_iter)
+    ref_phi = hist[0][-1]["phi"]
+    ds2 = S.random_problem(256, 20000, 77, lam=3.0)
+    for form in FORMS:
+        e1 = _errors(ms, oracle_mod, ds1, form, np.maximum(ds1.truth, np.float32(ds1.G)))
+        e2 = _errors(ms, oracle_mod, ds2, form, ds2.truth)
+        ctx = ms.Context(ds1, precision=form)
+        img, rep, _ = ctx.solve(torch.full((1, ds1.N, ds1.N), ds1.G, dtype=torch.float32, device="cuda"),
+                                ds1.n_iter)
+        ctx.close()
+        img = img.cpu().numpy().astype(np.float64)
+        own = oracle_mod.objective(P1, img)[0]
+        rows.append((form, e1, e2, np.linalg.norm(img - ref_img) / np.linalg.norm(ref_img),
+                     abs(rep.phi - own) / abs(own), abs(rep.phi - ref_phi) / abs(ref_phi)))
+    print("\nform        | cfg1 vis  chi2      grad      | solve image  phi(own)  phi(traj) | 256px vis  chi2      grad")
+    for form, e1, e2, im, po, pt in rows:
+        print(f"{form:11s} | {e1['vis']:.2e}  {e1['chi2']:.2e}  {e1['grad']:.2e} | {im:.2e}     {po:.2e}  {pt:.2e}  |"
+              f" {e2['vis']:.2e}   {e2['chi2']:.2e}  {e2['grad']:.2e}")
+    for form, e1, e2, im, po, pt in rows:
+        exact = form == "fp64_direct"
+        for e in (e1, e2):
+            assert e["vis"] <= (2e-7 if exact else 1e-5)
+            assert e["grad"] <= (2e-7 if exact else 1e-4)
+            assert e["chi2"] <= (1e-11 if exact else 1e-6)
+        assert im <= 1e-3
+        assert (pt if exact else po) <= 1e-6

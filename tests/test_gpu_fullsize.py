@@ -177,3 +177,34 @@ def test_config4_cube_batched_equals_single_channel(cfg4, ms):
     r = V[:, 0].astype(np.float64) + 1j * V[:, 1].astype(np.float64) - ds.vo
     chi_host = 0.5 * np.sum(np.abs(r) ** 2 / ds.sigma ** 2)
     assert abs(chi - chi_host) <= 1e-6 * chi_host
+
+
+def test_config5_forward_and_adjoint_sampled(ms, oracle_mod):
+    """1024 x 1024 image, 2.0e7 visibilities (four 256-column blocks per tile,
+    16 adjoint output blocks), FP16x3 in the default launch configuration:
+    sampled visibilities against the oracle's direct sum, and the adjoint of
+    an input that is non-zero on 20,000 visibilities on a 32 x 32 crop."""
+    import torch
+    ds = S.make(5)
+    ctx = ms.Context(ds, precision="fp16x3")
+    img = np.maximum(ds.truth, ds.G)
+    V = ctx.forward(torch.from_numpy(img).cuda()).cpu().numpy().astype(np.float64)
+    idx = _sample(ds.Z, 128, 51)
+    ref = oracle_mod.forward(ds.N, ds.dx, ds.dy, ds.u[idx], ds.v[idx],
+                             ds.pb[0].astype(np.float64) * img[0].astype(np.float64), "direct")
+    got = V[idx, 0] + 1j * V[idx, 1]
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 1e-5
+    del V
+    idx = _sample(ds.Z, 20000, 52)
+    t = S.random_complex(idx.size, 53)
+    y = np.zeros((ds.Z, 2), dtype=np.float32)
+    y[idx, 0], y[idx, 1] = t.real, t.imag
+    G = ctx.adjoint(torch.from_numpy(y).cuda()).cpu().numpy().astype(np.float64)[0]
+    for n0, m0 in [(500, 470), (3, 990)]:
+        ref = oracle_mod.adjoint(ds.N, ds.dx, ds.dy, ds.u[idx], ds.v[idx],
+                                 y[idx, 0].astype(np.float64) + 1j * y[idx, 1].astype(np.float64),
+                                 crop=(n0, 32, m0, 32))
+        ref = ref * ds.pb[0, n0:n0 + 32, m0:m0 + 32].astype(np.float64)
+        got = G[n0:n0 + 32, m0:m0 + 32]
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-4, (n0, m0)
+    ctx.close()
