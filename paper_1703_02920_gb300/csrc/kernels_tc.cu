@@ -39,6 +39,12 @@ namespace msk {
 // split-K partials at the end of each unit (once or twice per CTA).
 // ===========================================================================
 constexpr int ADJ_MAX_STAGES = 3;
+// Stages (of 16 visibilities) accumulated in TMEM before the accumulator is
+// drained into the unit's double-float partial.  The tensor core rounds each
+// MMA's addition into the FP32 accumulator toward zero, so an accumulation of
+// K MMAs shrinks by up to ~K ulp; bounding K (6 MMAs per stage) bounds that
+// bias at ~1e-5 relative however many visibilities a unit spans.
+constexpr int ADJ_DRAIN = 128;
 constexpr int ADJ_THREADS = 448;
 constexpr int ADJ_PRODUCER_WARPS = ADJ_THREADS / 32 - 1;  // every warp but the MMA warp
 
@@ -72,7 +78,7 @@ struct AdjShared {
 template <bool FROM_UV, bool F16, int ADJ_STAGES>
 __global__ void __launch_bounds__(ADJ_THREADS, 1)
     k_adj_tc(DevData d, const AdjUnit* __restrict__ units, const int* __restrict__ cta_unit_off,
-             const float2* __restrict__ y, const float* __restrict__ yscale, float* __restrict__ partial,
+             const float2* __restrict__ y, const float* __restrict__ yscale, float2* __restrict__ partial,
              uint64_t spin, int* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ AdjShared S;
@@ -114,13 +120,15 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             const uint32_t sbase = smem_u32(smem);
             uint32_t sc = 0;
             bool ok = true;
+            uint32_t it = 0;  // accumulation segments so far (tfull / tempty phases)
             for (int u = u0; u < u1 && ok; ++u) {
-                const int it = u - u0;
+              const int nst = (int)((units[u].count + TCA_BK - 1) / TCA_BK);
+              for (int seg0 = 0; seg0 < nst && ok; seg0 += ADJ_DRAIN, ++it) {
                 ok = mbar_wait(&S.tempty, (it & 1) ^ 1, spin, abort, status);
                 if (!ok) break;
                 tc_fence_after();
-                const int nst = (int)((units[u].count + TCA_BK - 1) / TCA_BK);
-                for (int ks = 0; ks < nst; ++ks, ++sc) {
+                const int seg1 = min(nst, seg0 + ADJ_DRAIN);
+                for (int ks = seg0; ks < seg1; ++ks, ++sc) {
                     const int s = sc % ADJ_STAGES;
                     ok = mbar_wait(&S.full[s], (sc / ADJ_STAGES) & 1, spin, abort, status);
                     if (!ok) break;
@@ -139,7 +147,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                         const uint64_t aim_h = smem_desc(A + 2 * a_plane + ao, lboA, 128);
                         const uint64_t aim_l = smem_desc(A + 3 * a_plane + ao, lboA, 128);
                         const uint32_t dt = tmem + (uint32_t)(mt * BLK);
-                        const uint32_t acc = ks > 0 ? 1u : 0u;
+                        const uint32_t acc = ks > seg0 ? 1u : 0u;
                         umma_bf16(dt, are_h, bre_h, idesc, acc);
                         umma_bf16(dt, are_h, bre_l, idesc, 1u);
                         umma_bf16(dt, are_l, bre_h, idesc, 1u);
@@ -150,6 +158,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                     umma_commit(&S.empty[s]);
                 }
                 if (ok) umma_commit(&S.tfull);
+              }
             }
             umma_commit(&S.drain);
             int dummy = 0;
@@ -167,7 +176,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
         const int jj = ptid & 15;           // visibility within the stage
         const int ngA = R / 8, ngB = BLK / 8;
         const float ysc = F16 ? yscale[0] : 1.f;
-        uint32_t sc = 0;
+        uint32_t sc = 0, dr = 0;  // stages produced; accumulator drains (warps 0-3)
         bool ok = true;
         for (int u = u0; u < u1 && ok; ++u) {
             const AdjUnit un = units[u];
@@ -269,36 +278,39 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.full[s]);
-            }
-            if (!ok || warp >= 4) continue;
-            // ------------------------- drain of unit u (warps 0-3, 128 threads)
-            ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull, (u - u0) & 1, spin, abort, status, 1024));
-            if (!ok) break;
-            tc_fence_after();
-            float* out = partial + (int64_t)u * BLK * BLK;
-            for (int mt = 0; mt < n_mt; ++mt) {
-                const int nrow = mt * 128 + warp * 32 + lane;
-                const uint32_t lb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * BLK);
-                for (int q = 0; q < BLK / 16; ++q) {
-                    uint32_t r[16];
-                    tmem_ld16(lb + q * 16, r);
-                    tmem_ld_wait();
-                    if (nrow < BLK) {
-                        float4* o = (float4*)(out + (int64_t)nrow * BLK + q * 16);
-                        o[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]),
-                                           __uint_as_float(r[2]), __uint_as_float(r[3]));
-                        o[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]),
-                                           __uint_as_float(r[6]), __uint_as_float(r[7]));
-                        o[2] = make_float4(__uint_as_float(r[8]), __uint_as_float(r[9]),
-                                           __uint_as_float(r[10]), __uint_as_float(r[11]));
-                        o[3] = make_float4(__uint_as_float(r[12]), __uint_as_float(r[13]),
-                                           __uint_as_float(r[14]), __uint_as_float(r[15]));
+                // warps 0-3 drain the accumulator after the last stage of each
+                // accumulation segment into the unit's double-float partial
+                if (warp < 4 && ((ks + 1) % ADJ_DRAIN == 0 || ks + 1 == nst)) {
+                    ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull, dr & 1, spin, abort, status, 1024));
+                    if (!ok) break;
+                    tc_fence_after();
+                    const bool first = ks < ADJ_DRAIN;
+                    float2* out = partial + (int64_t)u * BLK * BLK;
+                    for (int mt = 0; mt < n_mt; ++mt) {
+                        const int nrow = mt * 128 + warp * 32 + lane;
+                        const uint32_t lb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * BLK);
+                        for (int q = 0; q < BLK / 16; ++q) {
+                            uint32_t r[16];
+                            tmem_ld16(lb + q * 16, r);
+                            tmem_ld_wait();
+                            if (nrow < BLK) {
+                                float4* o = (float4*)(out + (int64_t)nrow * BLK + q * 16);  // 2 pairs each
+#pragma unroll
+                                for (int k = 0; k < 8; ++k) {
+                                    float4 v = first ? make_float4(0.f, 0.f, 0.f, 0.f) : o[k];
+                                    two_sum_acc(v.x, v.y, __uint_as_float(r[2 * k]));
+                                    two_sum_acc(v.z, v.w, __uint_as_float(r[2 * k + 1]));
+                                    o[k] = v;
+                                }
+                            }
+                        }
                     }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S.tempty);
+                    ++dr;
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.tempty);
         }
     }
 
@@ -312,7 +324,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
 
 template <bool FROM_UV, bool F16, int STAGES>
 static void launch_adj_variant(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                               const float2* y, const float* yscale, float* partial, uint64_t spin,
+                               const float2* y, const float* yscale, float2* partial, uint64_t spin,
                                int* status, cudaStream_t st) {
     const int smem = adj_tc_smem_bytes(d.N, STAGES);
     cudaFuncSetAttribute(k_adj_tc<FROM_UV, F16, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -321,7 +333,7 @@ static void launch_adj_variant(const DevData& d, const AdjUnit* units, const int
 }
 
 void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                   const float2* y, const float* yscale, float* partial, uint64_t spin, int* status,
+                   const float2* y, const float* yscale, float2* partial, uint64_t spin, int* status,
                    cudaStream_t st) {
     if (n_ctas <= 0) return;
     const bool s2 = d.adj_stages == 2;
@@ -335,7 +347,7 @@ void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* c
 }
 
 void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                      const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st) {
+                      const float2* y, float2* partial, uint64_t spin, int* status, cudaStream_t st) {
     if (n_ctas <= 0) return;
     launch_adj_variant<true, false, ADJ_MAX_STAGES>(d, units, cta_unit_off, n_ctas, y, nullptr, partial, spin,
                                                     status, st);
@@ -343,7 +355,7 @@ void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_uni
 
 // Single channel: out[p] = A[p] * (unit partials summed in unit order, FP64).
 __global__ void __launch_bounds__(256) k_adj_tc_reduce_out(int N, const int* __restrict__ cb_unit_off,
-                                                           const float* __restrict__ partial,
+                                                           const float2* __restrict__ partial,
                                                            const float* __restrict__ beam,
                                                            float* __restrict__ out) {
     const int64_t NN = (int64_t)N * N;
@@ -355,12 +367,15 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce_out(int N, const int* __r
     const int blk = (n / BLK) * nbx + m / BLK;
     const int64_t loc = (int64_t)(n % BLK) * BLK + (m % BLK);
     float s = 0.f, comp = 0.f;
-    for (int u = cb_unit_off[blk]; u < cb_unit_off[blk + 1]; ++u)
-        two_sum_acc(s, comp, __ldg(partial + (int64_t)u * BLK * BLK + loc));
+    for (int u = cb_unit_off[blk]; u < cb_unit_off[blk + 1]; ++u) {
+        const float2 q = __ldg(partial + (int64_t)u * BLK * BLK + loc);  // (hi, lo)
+        two_sum_acc(s, comp, q.x);
+        comp += q.y;
+    }
     out[p] = beam[p] * (s + comp);
 }
 
-void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partial, const float* beam,
+void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float2* partial, const float* beam,
                               float* out, cudaStream_t st) {
     k_adj_tc_reduce_out<<<prep_blocks(N), 256, 0, st>>>(N, cb_unit_off, partial, beam, out);
 }
@@ -368,7 +383,7 @@ void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partia
 // Sum the unit partials of each (channel, block) in unit order (FP64) into
 // gsum[c][N*N] (without the beam factor).
 __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __restrict__ cb_unit_off,
-                                                       const float* __restrict__ partial,
+                                                       const float2* __restrict__ partial,
                                                        const float* __restrict__ yscale,
                                                        double* __restrict__ gsum) {
     const int N = d.N;
@@ -384,25 +399,32 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __r
     const int cb = c * nbx * nbx + blk;
     const int u0 = cb_unit_off[cb], u1 = cb_unit_off[cb + 1];
     const int64_t stride = (int64_t)BLK * BLK;
-    const float* src = partial + loc;
-    // compensated FP32 sum in unit order (Neumaier); FP64 throughput on this
-    // part is too low for one FP64 add per partial
+    const float2* src = partial + loc;
+    // compensated FP32 sum of the double-float partials in unit order
+    // (Neumaier); FP64 throughput on this part is too low for FP64 adds
     float s = 0.f, comp = 0.f;
     int u = u0;
     for (; u + 8 <= u1; u += 8) {
-        float q[8];
+        float2 q[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) q[k] = __ldg(src + (int64_t)(u + k) * stride);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) two_sum_acc(s, comp, q[k]);
+        for (int k = 0; k < 8; ++k) {
+            two_sum_acc(s, comp, q[k].x);
+            comp += q[k].y;
+        }
     }
-    for (; u < u1; ++u) two_sum_acc(s, comp, __ldg(src + (int64_t)u * stride));
+    for (; u < u1; ++u) {
+        const float2 q = __ldg(src + (int64_t)u * stride);
+        two_sum_acc(s, comp, q.x);
+        comp += q.y;
+    }
     const double inv = yscale ? 1.0 / (double)yscale[0] : 1.0;
     gsum[(int64_t)c * NN + p] = ((double)s + (double)comp) * inv;
 }
 
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* cb_unit_off,
-                          const float* partial, const float* yscale, double* gsum, cudaStream_t st) {
+                          const float2* partial, const float* yscale, double* gsum, cudaStream_t st) {
     (void)units;
     dim3 grid(prep_blocks(d.N), d.C);
     k_adj_tc_reduce<<<grid, 256, 0, st>>>(d, cb_unit_off, partial, yscale, gsum);

@@ -208,3 +208,27 @@ def test_config5_forward_and_adjoint_sampled(ms, oracle_mod):
         got = G[n0:n0 + 32, m0:m0 + 32]
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-4, (n0, m0)
     ctx.close()
+
+
+@pytest.mark.parametrize("config, crop", [(2, 32), (5, 16)])
+def test_adjoint_full_data(ms, oracle_mod, config, crop):
+    """Every visibility non-zero (the weighted residual at the truth image),
+    so each CTA accumulates its whole share of the data set: the gradient
+    term against the oracle's adjoint over all Z visibilities on two pixel
+    crops.  This is where accumulation bias would show (it grows with the
+    visibilities a CTA sums)."""
+    import torch
+    ds = S.make(config)
+    ctx = ms.Context(ds, precision="fp16x3")
+    img = np.maximum(ds.truth, ds.G)
+    V = ctx.forward(torch.from_numpy(img).cuda()).cpu().numpy().astype(np.float64)
+    y = ((V[:, 0] + 1j * V[:, 1] - ds.vo) / ds.sigma ** 2).astype(np.complex64)
+    del V
+    G = ctx.adjoint(torch.from_numpy(np.stack([y.real, y.imag], 1)).cuda()).cpu().numpy().astype(np.float64)[0]
+    ctx.close()
+    for n0, m0 in [(ds.N // 2 - crop // 2, ds.N // 2 - crop // 2), (5, ds.N - crop - 9)]:
+        ref = oracle_mod.adjoint(ds.N, ds.dx, ds.dy, ds.u, ds.v, y.astype(np.complex128),
+                                 crop=(n0, crop, m0, crop))
+        ref = ref * ds.pb[0, n0:n0 + crop, m0:m0 + crop].astype(np.float64)
+        got = G[n0:n0 + crop, m0:m0 + crop]
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-4, (n0, m0)
