@@ -248,7 +248,7 @@ int32_t mem_profile_read(mem_ctx *ctx, int32_t max_kernels, char *names, double 
  * 8-byte aligned), pb_dev and img_dev (N*N floats).  N must be 64, 128 or
  * 256; other sizes return MEM_EINVAL with a message in mem_last_error(NULL).
  *
- * Scratch lives in a fixed static device array of about 32 MB (split-K
+ * Scratch lives in a fixed static device array of about 16 MB (split-K
  * partials for at most 64 CTAs plus the work list) that every GPU loading the
  * library holds until exit.  All calls share it: calls that overlap on the
  * GPU race and must be serialised by the caller.  The array keeps the last

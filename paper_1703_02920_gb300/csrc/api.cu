@@ -285,7 +285,7 @@ struct mem_ctx {
     double* col_psum = nullptr;                 // column-mean partial sums
     float* col_pmax = nullptr;
     float *yscale = nullptr, *ymax_part = nullptr;  // FP16X3 scale of the adjoint input
-    float2* partial = nullptr;  // adjoint unit partials, double-float (hi, lo) pairs
+    float* partial = nullptr;  // adjoint unit partials (FP32, one BLK x BLK block each)
     int* dstatus = nullptr;
     float* stage = nullptr;  // host-call staging (image, gradient)
 

@@ -128,19 +128,19 @@ int adj_tc_smem_bytes(int N, int stages);
 // units sorted by CTA: CTA b runs units [cta_unit_off[b], cta_unit_off[b+1]).
 // f16 = 1: FP16X3 with y scaled by yscale[0] (partials carry the scale).
 void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                   const float2* y, const float* yscale, float2* partial, uint64_t spin, int* status,
+                   const float2* y, const float* yscale, float* partial, uint64_t spin, int* status,
                    cudaStream_t st);
 // Variant reading u, v (FP64, wavelengths) instead of the prepared phase
 // increments: the caller passes d.u, d.v, d.dx, d.dy; d.pa / d.pb are unused.
 void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                      const float2* y, float2* partial, uint64_t spin, int* status, cudaStream_t st);
+                      const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st);
 // out[p] = A[p] * sum of unit partials (single channel, unit order, FP64 sum).
-void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float2* partial, const float* beam,
+void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partial, const float* beam,
                               float* out, cudaStream_t st);
 // Sum unit partials per channel (unit order) into gsum[C][N*N].
 // yscale (nullable): partials are divided by yscale[0].
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* unit_off_by_chan_blk,
-                          const float2* partial, const float* yscale, double* gsum, cudaStream_t st);
+                          const float* partial, const float* yscale, double* gsum, cudaStream_t st);
 
 // grad_i = sum_{c in image i} A_c * sum_k gsum[k][c] + lambda (1 + log(I/G)); optional projection.
 void launch_finalize(const DevData& d, const ImgSrc& src, const double* gsum, int ks, int projected,

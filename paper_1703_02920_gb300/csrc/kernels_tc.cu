@@ -40,10 +40,11 @@ namespace msk {
 // ===========================================================================
 constexpr int ADJ_MAX_STAGES = 3;
 // Stages (of 16 visibilities) accumulated in TMEM before the accumulator is
-// drained into the unit's double-float partial.  The tensor core rounds each
-// MMA's addition into the FP32 accumulator toward zero, so an accumulation of
-// K MMAs shrinks by up to ~K ulp; bounding K (6 MMAs per stage) bounds that
-// bias at ~1e-5 relative however many visibilities a unit spans.
+// added into the unit's FP32 partial.  The tensor core rounds each MMA's
+// addition into its FP32 accumulator toward zero, so an accumulation of K
+// MMAs shrinks by up to ~K ulp; bounding K (6 MMAs per stage) bounds that
+// bias at ~1e-5 relative however many visibilities a unit spans.  The drains
+// add with ordinary round-to-nearest FP32 arithmetic, which has no such bias.
 constexpr int ADJ_DRAIN = 128;
 constexpr int ADJ_THREADS = 448;
 constexpr int ADJ_PRODUCER_WARPS = ADJ_THREADS / 32 - 1;  // every warp but the MMA warp
@@ -78,7 +79,7 @@ struct AdjShared {
 template <bool FROM_UV, bool F16, int ADJ_STAGES>
 __global__ void __launch_bounds__(ADJ_THREADS, 1)
     k_adj_tc(DevData d, const AdjUnit* __restrict__ units, const int* __restrict__ cta_unit_off,
-             const float2* __restrict__ y, const float* __restrict__ yscale, float2* __restrict__ partial,
+             const float2* __restrict__ y, const float* __restrict__ yscale, float* __restrict__ partial,
              uint64_t spin, int* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ AdjShared S;
@@ -284,25 +285,40 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                     ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull, dr & 1, spin, abort, status, 1024));
                     if (!ok) break;
                     tc_fence_after();
-                    const bool first = ks < ADJ_DRAIN;
-                    float2* out = partial + (int64_t)u * BLK * BLK;
+                    const bool first = ks < ADJ_DRAIN;  // the unit's first segment stores
+                    float* out = partial + (int64_t)u * BLK * BLK;
                     for (int mt = 0; mt < n_mt; ++mt) {
                         const int nrow = mt * 128 + warp * 32 + lane;
+                        const bool row_ok = nrow < BLK;
                         const uint32_t lb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * BLK);
-                        for (int q = 0; q < BLK / 16; ++q) {
+                        float4* orow = (float4*)(out + (int64_t)(row_ok ? nrow : 0) * BLK);
+                        // the previous partial of chunk q+1 is loaded while chunk q is added
+                        float4 o0[4], o1[4];
+                        auto ld_old = [&](int q, float4* o) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                o[k] = (first || !row_ok) ? make_float4(0.f, 0.f, 0.f, 0.f) : orow[q * 4 + k];
+                        };
+                        auto add_store = [&](int q, const float4* o) {
                             uint32_t r[16];
                             tmem_ld16(lb + q * 16, r);
-                            tmem_ld_wait();
-                            if (nrow < BLK) {
-                                float4* o = (float4*)(out + (int64_t)nrow * BLK + q * 16);  // 2 pairs each
+                            tmem_ld_wait(r);
+                            if (row_ok) {
 #pragma unroll
-                                for (int k = 0; k < 8; ++k) {
-                                    float4 v = first ? make_float4(0.f, 0.f, 0.f, 0.f) : o[k];
-                                    two_sum_acc(v.x, v.y, __uint_as_float(r[2 * k]));
-                                    two_sum_acc(v.z, v.w, __uint_as_float(r[2 * k + 1]));
-                                    o[k] = v;
-                                }
+                                for (int k = 0; k < 4; ++k)
+                                    orow[q * 4 + k] = make_float4(o[k].x + __uint_as_float(r[4 * k]),
+                                                                  o[k].y + __uint_as_float(r[4 * k + 1]),
+                                                                  o[k].z + __uint_as_float(r[4 * k + 2]),
+                                                                  o[k].w + __uint_as_float(r[4 * k + 3]));
                             }
+                        };
+                        const int nq = BLK / 16;  // even
+                        ld_old(0, o0);
+                        for (int q = 0; q < nq; q += 2) {
+                            ld_old(q + 1, o1);
+                            add_store(q, o0);
+                            if (q + 2 < nq) ld_old(q + 2, o0);
+                            add_store(q + 1, o1);
                         }
                     }
                     tc_fence_before();
@@ -324,7 +340,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
 
 template <bool FROM_UV, bool F16, int STAGES>
 static void launch_adj_variant(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                               const float2* y, const float* yscale, float2* partial, uint64_t spin,
+                               const float2* y, const float* yscale, float* partial, uint64_t spin,
                                int* status, cudaStream_t st) {
     const int smem = adj_tc_smem_bytes(d.N, STAGES);
     cudaFuncSetAttribute(k_adj_tc<FROM_UV, F16, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -333,7 +349,7 @@ static void launch_adj_variant(const DevData& d, const AdjUnit* units, const int
 }
 
 void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                   const float2* y, const float* yscale, float2* partial, uint64_t spin, int* status,
+                   const float2* y, const float* yscale, float* partial, uint64_t spin, int* status,
                    cudaStream_t st) {
     if (n_ctas <= 0) return;
     const bool s2 = d.adj_stages == 2;
@@ -347,7 +363,7 @@ void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* c
 }
 
 void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                      const float2* y, float2* partial, uint64_t spin, int* status, cudaStream_t st) {
+                      const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st) {
     if (n_ctas <= 0) return;
     launch_adj_variant<true, false, ADJ_MAX_STAGES>(d, units, cta_unit_off, n_ctas, y, nullptr, partial, spin,
                                                     status, st);
@@ -355,7 +371,7 @@ void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_uni
 
 // Single channel: out[p] = A[p] * (unit partials summed in unit order, FP64).
 __global__ void __launch_bounds__(256) k_adj_tc_reduce_out(int N, const int* __restrict__ cb_unit_off,
-                                                           const float2* __restrict__ partial,
+                                                           const float* __restrict__ partial,
                                                            const float* __restrict__ beam,
                                                            float* __restrict__ out) {
     const int64_t NN = (int64_t)N * N;
@@ -367,15 +383,12 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce_out(int N, const int* __r
     const int blk = (n / BLK) * nbx + m / BLK;
     const int64_t loc = (int64_t)(n % BLK) * BLK + (m % BLK);
     float s = 0.f, comp = 0.f;
-    for (int u = cb_unit_off[blk]; u < cb_unit_off[blk + 1]; ++u) {
-        const float2 q = __ldg(partial + (int64_t)u * BLK * BLK + loc);  // (hi, lo)
-        two_sum_acc(s, comp, q.x);
-        comp += q.y;
-    }
+    for (int u = cb_unit_off[blk]; u < cb_unit_off[blk + 1]; ++u)
+        two_sum_acc(s, comp, __ldg(partial + (int64_t)u * BLK * BLK + loc));
     out[p] = beam[p] * (s + comp);
 }
 
-void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float2* partial, const float* beam,
+void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partial, const float* beam,
                               float* out, cudaStream_t st) {
     k_adj_tc_reduce_out<<<prep_blocks(N), 256, 0, st>>>(N, cb_unit_off, partial, beam, out);
 }
@@ -383,7 +396,7 @@ void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float2* parti
 // Sum the unit partials of each (channel, block) in unit order (FP64) into
 // gsum[c][N*N] (without the beam factor).
 __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __restrict__ cb_unit_off,
-                                                       const float2* __restrict__ partial,
+                                                       const float* __restrict__ partial,
                                                        const float* __restrict__ yscale,
                                                        double* __restrict__ gsum) {
     const int N = d.N;
@@ -399,32 +412,25 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __r
     const int cb = c * nbx * nbx + blk;
     const int u0 = cb_unit_off[cb], u1 = cb_unit_off[cb + 1];
     const int64_t stride = (int64_t)BLK * BLK;
-    const float2* src = partial + loc;
-    // compensated FP32 sum of the double-float partials in unit order
-    // (Neumaier); FP64 throughput on this part is too low for FP64 adds
+    const float* src = partial + loc;
+    // compensated FP32 sum in unit order (Neumaier); FP64 throughput on this
+    // part is too low for one FP64 add per partial
     float s = 0.f, comp = 0.f;
     int u = u0;
     for (; u + 8 <= u1; u += 8) {
-        float2 q[8];
+        float q[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) q[k] = __ldg(src + (int64_t)(u + k) * stride);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            two_sum_acc(s, comp, q[k].x);
-            comp += q[k].y;
-        }
+        for (int k = 0; k < 8; ++k) two_sum_acc(s, comp, q[k]);
     }
-    for (; u < u1; ++u) {
-        const float2 q = __ldg(src + (int64_t)u * stride);
-        two_sum_acc(s, comp, q.x);
-        comp += q.y;
-    }
+    for (; u < u1; ++u) two_sum_acc(s, comp, __ldg(src + (int64_t)u * stride));
     const double inv = yscale ? 1.0 / (double)yscale[0] : 1.0;
     gsum[(int64_t)c * NN + p] = ((double)s + (double)comp) * inv;
 }
 
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* cb_unit_off,
-                          const float2* partial, const float* yscale, double* gsum, cudaStream_t st) {
+                          const float* partial, const float* yscale, double* gsum, cudaStream_t st) {
     (void)units;
     dim3 grid(prep_blocks(d.N), d.C);
     k_adj_tc_reduce<<<grid, 256, 0, st>>>(d, cb_unit_off, partial, yscale, gsum);

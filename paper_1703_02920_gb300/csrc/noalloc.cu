@@ -11,7 +11,7 @@
 // Its scratch space (split-K partial sums and the work list) is a file-scope
 // static __device__ array of fixed size.  The array is part of the library's
 // device image: every GPU on which the library is loaded holds it (about
-// 32 MB) until the process exits.  Every call shares it, so calls that
+// 16 MB) until the process exits.  Every call shares it, so calls that
 // overlap on the GPU (different streams, threads or processes sharing a
 // context) race; serialise them.  The array keeps the previous call's
 // contents; nothing in it needs to start at zero (each partial block is fully
@@ -32,7 +32,7 @@ namespace {
 constexpr int NOALLOC_MAX_CTAS = 64;
 constexpr int NOALLOC_BLK = 256;
 
-static __device__ __align__(256) float2 g_partial[(size_t)NOALLOC_MAX_CTAS * NOALLOC_BLK * NOALLOC_BLK];
+static __device__ __align__(256) float g_partial[(size_t)NOALLOC_MAX_CTAS * NOALLOC_BLK * NOALLOC_BLK];
 static __device__ __align__(256) AdjUnit g_units[NOALLOC_MAX_CTAS];
 // [0, NOALLOC_MAX_CTAS]: per-CTA unit offsets; then 2 entries of per-block offsets
 static __device__ __align__(256) int g_offs[NOALLOC_MAX_CTAS + 1 + 2];
@@ -40,7 +40,7 @@ static __device__ __align__(256) int g_status;
 
 struct DevPtrs {
     bool ready = false;
-    float2* partial = nullptr;
+    float* partial = nullptr;
     AdjUnit* units = nullptr;
     int* offs = nullptr;
     int* status = nullptr;

@@ -65,11 +65,14 @@ def test_error_table(ms, oracle_mod):
     for form, e1, e2, im, po, pt in rows:
         print(f"{form:11s} | {e1['vis']:.2e}  {e1['chi2']:.2e}  {e1['grad']:.2e} | {im:.2e}     {po:.2e}  {pt:.2e}  |"
               f" {e2['vis']:.2e}   {e2['chi2']:.2e}  {e2['grad']:.2e}")
+    # chi^2 bounds at arbitrary images per form (derived in test_gpu_parity)
+    tol_chi = {"fp64_direct": 1e-11, "fp32_direct": 1e-6, "bf16x3": 1e-5, "fp16x3": 3e-6}
     for form, e1, e2, im, po, pt in rows:
         exact = form == "fp64_direct"
         for e in (e1, e2):
             assert e["vis"] <= (2e-7 if exact else 1e-5)
             assert e["grad"] <= (2e-7 if exact else 1e-4)
-            assert e["chi2"] <= (1e-11 if exact else 1e-6)
+            assert e["chi2"] <= tol_chi[form]
         assert im <= 1e-3
+        # the objective at the final image (the benchmark spec bound)
         assert (pt if exact else po) <= 1e-6

@@ -20,7 +20,14 @@ pytestmark = pytest.mark.gpu
 # float32 through the ABI, so it agrees to float32 rounding of its outputs.
 TOL_V = {"fp64_direct": 2e-7, "fp32_direct": 1e-5, "bf16x3": 1e-5, "fp16x3": 1e-5}
 TOL_G = {"fp64_direct": 2e-7, "fp32_direct": 1e-4, "bf16x3": 1e-4, "fp16x3": 1e-4}
-TOL_PHI = {"fp64_direct": 1e-11, "fp32_direct": 1e-6, "bf16x3": 1e-6, "fp16x3": 1e-6}
+# chi^2 and Phi at a given image.  The objective bound of 1e-6 is held at
+# the solve's final image (test_gpu_solver); at arbitrary images, where the
+# model can dominate the residual (R = sum w Re(conj(r) V) / sum w |r|^2 near
+# 1), chi^2 moves by about 2R times a relative model bias:
+#   FP16x3: up to 3N/16 = 48 truncating accumulations per output at N = 256,
+#           ~1.4e-6 relative worst case, so 3e-6;
+#   BF16x3: the 8+8-bit table split leaves up to 2^-17 per entry, so 1e-5.
+TOL_PHI = {"fp64_direct": 1e-11, "fp32_direct": 1e-6, "bf16x3": 1e-5, "fp16x3": 3e-6}
 TOL_CHI = TOL_PHI
 FORMS = ["fp64_direct", "fp32_direct", "bf16x3", "fp16x3"]
 
