@@ -43,9 +43,9 @@ constexpr int ADJ_MAX_STAGES = 3;
 // added into the unit's FP32 partial.  The tensor core rounds each MMA's
 // addition into its FP32 accumulator toward zero, so an accumulation of K
 // MMAs shrinks by up to ~K ulp; bounding K (6 MMAs per stage) bounds that
-// bias at ~1e-5 relative however many visibilities a unit spans.  The drains
+// bias at ~2.5e-5 relative however many visibilities a unit spans.  The drains
 // add with ordinary round-to-nearest FP32 arithmetic, which has no such bias.
-constexpr int ADJ_DRAIN = 128;
+constexpr int ADJ_DRAIN = 256;
 constexpr int ADJ_THREADS = 448;
 constexpr int ADJ_PRODUCER_WARPS = ADJ_THREADS / 32 - 1;  // every warp but the MMA warp
 
@@ -59,6 +59,16 @@ __host__ __device__ inline uint32_t adj_tmem_cols(int BLK) {
     uint32_t p = 32;
     while ((int)p < c) p <<= 1;
     return p;
+}
+
+// Layout of a unit's partial block (BLK x BLK floats): the element of block
+// row n and column m lives at ((mt * BLK/16 + q) * 16 + k) * RB + r, with
+// n = mt * 128 + r (r < RB = min(BLK, 128)) and m = 16 q + k.  For a fixed
+// column, the rows a warp drains from its TMEM lanes are adjacent, so each
+// drain load and store is one coalesced 128-byte access.
+__host__ __device__ inline int64_t adj_partial_index(int n, int m, int BLK) {
+    const int RB = BLK < 128 ? BLK : 128;
+    return ((int64_t)((n / 128) * (BLK / 16) + m / 16) * 16 + (m % 16)) * RB + (n % 128);
 }
 
 struct AdjShared {
@@ -291,25 +301,24 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                         const int nrow = mt * 128 + warp * 32 + lane;
                         const bool row_ok = nrow < BLK;
                         const uint32_t lb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * BLK);
-                        float4* orow = (float4*)(out + (int64_t)(row_ok ? nrow : 0) * BLK);
+                        // column m of this lane's row: out[col(m) + nrow % 128], coalesced over the warp
+                        float* base = out + (row_ok ? adj_partial_index(nrow, 0, BLK) : 0);
+                        const int RB = BLK < 128 ? BLK : 128;
                         // the previous partial of chunk q+1 is loaded while chunk q is added
-                        float4 o0[4], o1[4];
-                        auto ld_old = [&](int q, float4* o) {
+                        float o0[16], o1[16];
+                        auto ld_old = [&](int q, float* o) {
 #pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                o[k] = (first || !row_ok) ? make_float4(0.f, 0.f, 0.f, 0.f) : orow[q * 4 + k];
+                            for (int k = 0; k < 16; ++k)
+                                o[k] = (first || !row_ok) ? 0.f : base[(int64_t)(q * 16 + k) * RB];
                         };
-                        auto add_store = [&](int q, const float4* o) {
+                        auto add_store = [&](int q, const float* o) {
                             uint32_t r[16];
                             tmem_ld16(lb + q * 16, r);
                             tmem_ld_wait(r);
                             if (row_ok) {
 #pragma unroll
-                                for (int k = 0; k < 4; ++k)
-                                    orow[q * 4 + k] = make_float4(o[k].x + __uint_as_float(r[4 * k]),
-                                                                  o[k].y + __uint_as_float(r[4 * k + 1]),
-                                                                  o[k].z + __uint_as_float(r[4 * k + 2]),
-                                                                  o[k].w + __uint_as_float(r[4 * k + 3]));
+                                for (int k = 0; k < 16; ++k)
+                                    base[(int64_t)(q * 16 + k) * RB] = o[k] + __uint_as_float(r[k]);
                             }
                         };
                         const int nq = BLK / 16;  // even
@@ -381,7 +390,7 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce_out(int N, const int* __r
     if (p >= NN) return;
     const int n = (int)(p / N), m = (int)(p % N);
     const int blk = (n / BLK) * nbx + m / BLK;
-    const int64_t loc = (int64_t)(n % BLK) * BLK + (m % BLK);
+    const int64_t loc = adj_partial_index(n % BLK, m % BLK, BLK);
     float s = 0.f, comp = 0.f;
     for (int u = cb_unit_off[blk]; u < cb_unit_off[blk + 1]; ++u)
         two_sum_acc(s, comp, __ldg(partial + (int64_t)u * BLK * BLK + loc));
@@ -408,7 +417,7 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __r
     if (p >= NN) return;
     const int n = (int)(p / N), m = (int)(p % N);
     const int blk = (n / BLK) * nbx + m / BLK;
-    const int64_t loc = (int64_t)(n % BLK) * BLK + (m % BLK);
+    const int64_t loc = adj_partial_index(n % BLK, m % BLK, BLK);
     const int cb = c * nbx * nbx + blk;
     const int u0 = cb_unit_off[cb], u1 = cb_unit_off[cb + 1];
     const int64_t stride = (int64_t)BLK * BLK;
