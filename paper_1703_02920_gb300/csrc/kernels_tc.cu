@@ -71,6 +71,18 @@ __host__ __device__ inline int64_t adj_partial_index(int n, int m, int BLK) {
     return ((int64_t)((n / 128) * (BLK / 16) + m / 16) * 16 + (m % 16)) * RB + (n % 128);
 }
 
+// Inverse of adj_partial_index: block row and column of partial element i.
+__host__ __device__ inline void adj_partial_rc(int64_t i, int BLK, int& n, int& m) {
+    const int RB = BLK < 128 ? BLK : 128;
+    const int r = (int)(i % RB);
+    int64_t t = i / RB;
+    const int k = (int)(t % 16);
+    t /= 16;
+    const int q = (int)(t % (BLK / 16)), mt = (int)(t / (BLK / 16));
+    n = mt * 128 + r;
+    m = q * 16 + k;
+}
+
 struct AdjShared {
     uint64_t full[ADJ_MAX_STAGES];
     uint64_t empty[ADJ_MAX_STAGES];
@@ -386,11 +398,14 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce_out(int N, const int* __r
     const int64_t NN = (int64_t)N * N;
     const int BLK = N < 256 ? N : 256;
     const int nbx = N / BLK;
-    const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (p >= NN) return;
-    const int n = (int)(p / N), m = (int)(p % N);
-    const int blk = (n / BLK) * nbx + m / BLK;
-    const int64_t loc = adj_partial_index(n % BLK, m % BLK, BLK);
+    // threads run over the partials' layout (coalesced reads); p is the pixel
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= NN) return;
+    const int blk = (int)(i / ((int64_t)BLK * BLK));
+    const int64_t loc = i % ((int64_t)BLK * BLK);
+    int nl, ml;
+    adj_partial_rc(loc, BLK, nl, ml);
+    const int64_t p = (int64_t)((blk / nbx) * BLK + nl) * N + (blk % nbx) * BLK + ml;
     float s = 0.f, comp = 0.f;
     for (int u = cb_unit_off[blk]; u < cb_unit_off[blk + 1]; ++u)
         two_sum_acc(s, comp, __ldg(partial + (int64_t)u * BLK * BLK + loc));
@@ -413,11 +428,14 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __r
     const int BLK = N < 256 ? N : 256;
     const int nbx = N / BLK;
     const int c = blockIdx.y;
-    const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (p >= NN) return;
-    const int n = (int)(p / N), m = (int)(p % N);
-    const int blk = (n / BLK) * nbx + m / BLK;
-    const int64_t loc = adj_partial_index(n % BLK, m % BLK, BLK);
+    // threads run over the partials' layout (coalesced reads); p is the pixel
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= NN) return;
+    const int blk = (int)(i / ((int64_t)BLK * BLK));
+    const int64_t loc = i % ((int64_t)BLK * BLK);
+    int nl, ml;
+    adj_partial_rc(loc, BLK, nl, ml);
+    const int64_t p = (int64_t)((blk / nbx) * BLK + nl) * N + (blk % nbx) * BLK + ml;
     const int cb = c * nbx * nbx + blk;
     const int u0 = cb_unit_off[cb], u1 = cb_unit_off[cb + 1];
     const int64_t stride = (int64_t)BLK * BLK;
