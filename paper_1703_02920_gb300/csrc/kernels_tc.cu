@@ -83,6 +83,35 @@ __host__ __device__ inline void adj_partial_rc(int64_t i, int BLK, int& n, int& 
     m = q * 16 + k;
 }
 
+// Drain of the TMEM accumulator by warps 0-3 (TMEM lane quadrant = warp):
+// partial (one unit's block, layout above) = [partial +] accumulator.  Kept
+// out of line so that its registers do not add to the producers' loop.
+__device__ __noinline__ void adj_drain(uint32_t tmem, float* out, int BLK, int n_mt, int warp, int lane,
+                                       bool first) {
+    const int RB = BLK < 128 ? BLK : 128;
+    for (int mt = 0; mt < n_mt; ++mt) {
+        const int nrow = mt * 128 + warp * 32 + lane;
+        const bool row_ok = nrow < BLK;
+        const uint32_t lb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * BLK);
+        // column m of this lane's row: base[m * RB], coalesced over the warp
+        float* base = out + (row_ok ? adj_partial_index(nrow, 0, BLK) : 0);
+        // per 16-column chunk: the TMEM load and the previous partial's loads
+        // are in flight together
+        for (int q = 0; q < BLK / 16; ++q) {
+            uint32_t r[16];
+            tmem_ld16(lb + q * 16, r);
+            float o[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) o[k] = (first || !row_ok) ? 0.f : base[(int64_t)(q * 16 + k) * RB];
+            tmem_ld_wait(r);
+            if (row_ok) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) base[(int64_t)(q * 16 + k) * RB] = o[k] + __uint_as_float(r[k]);
+            }
+        }
+    }
+}
+
 struct AdjShared {
     uint64_t full[ADJ_MAX_STAGES];
     uint64_t empty[ADJ_MAX_STAGES];
@@ -225,7 +254,9 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             uint64_t na, nb;
             float2 ny;
             fetch(0, na, nb, ny);
-            for (int ks = 0; ks < nst; ++ks, ++sc) {
+          for (int seg0 = 0; seg0 < nst && ok; seg0 += ADJ_DRAIN) {
+            const int seg1 = min(nst, seg0 + ADJ_DRAIN);
+            for (int ks = seg0; ks < seg1; ++ks, ++sc) {
                 const int s = sc % ADJ_STAGES;
                 const uint64_t pa = na, pb = nb;
                 const cf2 yv = {ny.x * ysc, ny.y * ysc};
@@ -301,53 +332,20 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.full[s]);
-                // warps 0-3 drain the accumulator after the last stage of each
-                // accumulation segment into the unit's double-float partial
-                if (warp < 4 && ((ks + 1) % ADJ_DRAIN == 0 || ks + 1 == nst)) {
-                    ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull, dr & 1, spin, abort, status, 1024));
-                    if (!ok) break;
-                    tc_fence_after();
-                    const bool first = ks < ADJ_DRAIN;  // the unit's first segment stores
-                    float* out = partial + (int64_t)u * BLK * BLK;
-                    for (int mt = 0; mt < n_mt; ++mt) {
-                        const int nrow = mt * 128 + warp * 32 + lane;
-                        const bool row_ok = nrow < BLK;
-                        const uint32_t lb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * BLK);
-                        // column m of this lane's row: out[col(m) + nrow % 128], coalesced over the warp
-                        float* base = out + (row_ok ? adj_partial_index(nrow, 0, BLK) : 0);
-                        const int RB = BLK < 128 ? BLK : 128;
-                        // the previous partial of chunk q+1 is loaded while chunk q is added
-                        float o0[16], o1[16];
-                        auto ld_old = [&](int q, float* o) {
-#pragma unroll
-                            for (int k = 0; k < 16; ++k)
-                                o[k] = (first || !row_ok) ? 0.f : base[(int64_t)(q * 16 + k) * RB];
-                        };
-                        auto add_store = [&](int q, const float* o) {
-                            uint32_t r[16];
-                            tmem_ld16(lb + q * 16, r);
-                            tmem_ld_wait(r);
-                            if (row_ok) {
-#pragma unroll
-                                for (int k = 0; k < 16; ++k)
-                                    base[(int64_t)(q * 16 + k) * RB] = o[k] + __uint_as_float(r[k]);
-                            }
-                        };
-                        const int nq = BLK / 16;  // even
-                        ld_old(0, o0);
-                        for (int q = 0; q < nq; q += 2) {
-                            ld_old(q + 1, o1);
-                            add_store(q, o0);
-                            if (q + 2 < nq) ld_old(q + 2, o0);
-                            add_store(q + 1, o1);
-                        }
-                    }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&S.tempty);
-                    ++dr;
-                }
             }
+            // warps 0-3 drain the accumulator after the last stage of each
+            // accumulation segment into the unit's partial
+            if (!ok || warp >= 4) continue;
+            ok = __all_sync(0xffffffffu, mbar_wait(&S.tfull, dr & 1, spin, abort, status, 1024));
+            if (!ok) break;
+            tc_fence_after();
+            adj_drain(tmem, partial + (int64_t)u * BLK * BLK, BLK, n_mt, warp, lane,
+                      seg0 == 0 /* the unit's first segment stores */);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.tempty);
+            ++dr;
+          }
         }
     }
 
