@@ -55,10 +55,11 @@ def _peaks():
 class ClockSampler:
     """nvidia-smi samples during the timed region."""
 
-    def __init__(self, gpu: int):
+    def __init__(self, gpu: int, path: str | None = None):
+        import tempfile
         self.gpu = gpu
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"memsynth_clocks_gpu{gpu}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -204,6 +205,7 @@ def main():
     ap.add_argument("--precision", default="fp16x3", choices=["bf16x3", "fp16x3", "fp32_direct", "fp64_direct"])
     ap.add_argument("--solve-iters", type=int, default=4)
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--clock-log", default=None, help="CSV file for the nvidia-smi samples (default: a temp file)")
     ap.add_argument("--tiling", default=None,
                     help="kernel,cols,fwd_stages,adj_stages (e.g. resident,256,6,3): fixed tiling, no autotuning")
     ap.add_argument("--profile-run", action="store_true",
@@ -270,7 +272,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = ctx.launches()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clock_log) as clk:
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)

@@ -86,7 +86,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     path = _build.LIB
     if not os.path.exists(path) or not _build.up_to_date():
         if not build_if_missing:
-            raise RuntimeError(f"libmemsynth is not built ({path}); call __graft_entry__.build()")
+            raise RuntimeError(f"libmemsynth is not built ({path}); run python -m paper_1703_02920_gb300.build")
         _build.build()
     lib = ctypes.CDLL(path)
     P, D, I32, I64, V = ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p

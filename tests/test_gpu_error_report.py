@@ -74,5 +74,5 @@ def test_error_table(ms, oracle_mod):
             assert e["grad"] <= (2e-7 if exact else 1e-4)
             assert e["chi2"] <= tol_chi[form]
         assert im <= 1e-3
-        # the objective at the final image (the benchmark spec bound)
+        # the objective at the final image: the stated 1e-6 objective bound
         assert (pt if exact else po) <= 1e-6
