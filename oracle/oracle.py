@@ -97,6 +97,37 @@ def forward(N: int, dx: float, dy: float, u, v, B, form: str = "factored") -> np
     return out[0::2] + 1j * out[1::2]
 
 
+def forward_gridded(N: int, dx: float, dy: float, u, v, B, pad: int = 2) -> np.ndarray:
+    """The paper's gridded approximation of Eq. (1) (Section 2.4, the steps of
+    the objective evaluation; Algorithm alg:chi2gpu): the attenuated image B
+    is zero-padded to M = pad N (image centred), Fourier transformed on the
+    grid, modulated so that the phase centre is pixel (N/2, N/2), and the model
+    visibility is bilinearly interpolated at the sample's grid coordinates
+    (u M dx, v M dy).  Reading of the garbled modulation factor: on the grid
+    frequency (k, l) / (M dx, M dy) the exact sum equals FFT[l, k] (-1)^(k+l),
+    because pixel m sits at x = (m + M/2 - N/2 - M/2) dx in the centred padding.
+    complex128 (Z,)."""
+    u, v, B = _f64(u), _f64(v), _f64(B).reshape(N, N)
+    M = pad * N
+    o = (M - N) // 2
+    P = np.zeros((M, M))
+    P[o:o + N, o:o + N] = B
+    F = np.fft.fft2(P)  # F[l, k] = sum P[n', m'] exp(-2 pi i (l n' + k m') / M)
+
+    def grid(k, l):
+        sign = 1.0 - 2.0 * ((k + l) & 1)  # (-1)^(k+l), the phase-centre modulation
+        return F[l % M, k % M] * sign
+
+    out = np.zeros(u.size, dtype=np.complex128)
+    for j in range(u.size):
+        gu, gv = u[j] * M * dx, v[j] * M * dy
+        k0, l0 = int(np.floor(gu)), int(np.floor(gv))
+        fx, fy = gu - k0, gv - l0
+        out[j] = ((1 - fx) * (1 - fy) * grid(k0, l0) + fx * (1 - fy) * grid(k0 + 1, l0)
+                  + (1 - fx) * fy * grid(k0, l0 + 1) + fx * fy * grid(k0 + 1, l0 + 1))
+    return out
+
+
 def adjoint(N: int, dx: float, dy: float, u, v, y, crop=None, form: str = "factored") -> np.ndarray:
     """G[n,m] = sum_k Re(y_k exp(+2 pi i (u_k x_m + v_k y_n))) on a crop
     (n0, nn, m0, nm) of the image (default: the whole image), float64."""

@@ -345,3 +345,66 @@ def test_polish_is_continuous_in_the_start(oracle_mod):
     a = oracle_mod.polish(f, xs * (1 - 1e-3), f(xs * (1 - 1e-3)), h)
     b = oracle_mod.polish(f, xs * (1 + 1e-3), f(xs * (1 + 1e-3)), h)
     assert abs(a - b) <= 2e-5 * xs
+
+
+# ---------------------------------------------------------------------------
+# the paper's gridded forward (Section 2.4 steps, Algorithm alg:chi2gpu)
+# ---------------------------------------------------------------------------
+def _gridded_case(N=16, seed=3):
+    rng = np.random.default_rng(seed)
+    dx, dy = 1.3e-6, 0.9e-6
+    B = rng.random((N, N))
+    return N, dx, dy, B, rng
+
+
+def test_gridded_forward_on_grid_points_equals_the_direct_sum(oracle_mod):
+    """At grid frequencies (k, l) / (M dx, M dy) there is no interpolation:
+    FFT plus modulation must reproduce the direct sum of Eq. (1)."""
+    N, dx, dy, B, rng = _gridded_case()
+    for pad in (1, 2, 3):
+        M = pad * N
+        k = rng.integers(-M, M, 40)
+        l = rng.integers(-M, M, 40)
+        u, v = k / (M * dx), l / (M * dy)
+        g = oracle_mod.forward_gridded(N, dx, dy, u, v, B, pad)
+        d = oracle_mod.forward(N, dx, dy, u, v, B, "direct")
+        assert np.max(np.abs(g - d)) <= 1e-12 * np.max(np.abs(d)), pad
+
+
+def test_gridded_forward_is_the_bilinear_blend_of_grid_values(oracle_mod):
+    """Between grid points the result is the bilinear blend of the exact sums
+    at the four surrounding grid frequencies."""
+    N, dx, dy, B, rng = _gridded_case(seed=4)
+    pad = 2
+    M = pad * N
+    gu, gv = rng.uniform(-M, M, 30), rng.uniform(-M, M, 30)
+    u, v = gu / (M * dx), gv / (M * dy)
+    g = oracle_mod.forward_gridded(N, dx, dy, u, v, B, pad)
+    k0, l0 = np.floor(gu), np.floor(gv)
+    fx, fy = gu - k0, gv - l0
+    corner = lambda dk, dl: oracle_mod.forward(N, dx, dy, (k0 + dk) / (M * dx), (l0 + dl) / (M * dy), B, "direct")
+    ref = ((1 - fx) * (1 - fy) * corner(0, 0) + fx * (1 - fy) * corner(1, 0)
+           + (1 - fx) * fy * corner(0, 1) + fx * fy * corner(1, 1))
+    assert np.max(np.abs(g - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_gridded_forward_is_hermitian_and_converges_with_padding(oracle_mod):
+    """Real image: V(-u,-v) = conj V(u,v); the interpolation error against the
+    exact sum falls as the grid is refined by zero padding (smooth image)."""
+    N = 32
+    dx = dy = 1e-6
+    yy, xx = np.mgrid[0:N, 0:N] - N / 2
+    B = np.exp(-(xx ** 2 + yy ** 2) / (2 * 3.0 ** 2))
+    rng = np.random.default_rng(5)
+    r = rng.uniform(0, 0.45 / dx, 200)
+    t = rng.uniform(0, 2 * np.pi, 200)
+    u, v = r * np.cos(t), r * np.sin(t)
+    d = oracle_mod.forward(N, dx, dy, u, v, B, "direct")
+    errs = []
+    for pad in (1, 2, 4, 8):
+        g = oracle_mod.forward_gridded(N, dx, dy, u, v, B, pad)
+        gm = oracle_mod.forward_gridded(N, dx, dy, -u, -v, B, pad)
+        assert np.max(np.abs(gm - np.conj(g))) <= 1e-12 * np.max(np.abs(g))
+        errs.append(np.max(np.abs(g - d)) / np.max(np.abs(d)))
+    assert errs[0] > errs[1] > errs[2] > errs[3], errs
+    assert errs[3] < 0.05 * errs[0], errs
