@@ -338,6 +338,29 @@ def main():
     kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1],
                    "share": v[0] / max(sum(x[0] for x in kprof.values()), 1e-30)} for k, v in kprof.items()}
 
+    # ---- the paper's gridded forward (FFT + bilinear) beside the exact one:
+    # time per pass and its error against the exact model visibilities
+    gridded = None
+    if not args.no_solve:
+        vex = ctx.forward(img).double()
+        gridded = {}
+        for pad in (2, 4):
+            vg = ctx.forward_gridded(img, pad)  # warm-up (plan, buffers)
+            torch.cuda.synchronize()
+            gms = []
+            for _ in range(5):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                memsynth.mem_forward_gridded(ctx.handle, img, pad, vg)
+                b.record(stream)
+                torch.cuda.synchronize()
+                gms.append(a.elapsed_time(b))
+            err = float((vg.double() - vex).norm(dim=1).max() / vex.norm(dim=1).max())
+            gridded[f"pad{pad}"] = {"ms": statistics.mean(gms), "max_rel_err_vs_exact": err}
+        gridded["exact_forward_ms"] = kprof.get("fwd_tc", kprof.get("fwd_rs", (0.0, 1)))[0] / max(
+            kprof.get("fwd_tc", kprof.get("fwd_rs", (0.0, 1)))[1], 1)
+
     # ---- MEM solve from I = G: a few CG iterations in this form and in the
     # FP64 direct form (same algorithm, same start)
     solve = None
@@ -387,7 +410,7 @@ def main():
                         "d2h_bytes_per_step": int(img.numel() * 4 + 24)},
                 "gpu_launches": launches,
                 "roofline": roof, "kernels": kernels,
-                "clocks": clk.summary(), "cpu_baseline": cpu, "solve": solve}
+                "clocks": clk.summary(), "cpu_baseline": cpu, "solve": solve, "gridded_forward": gridded}
         print(json.dumps(line))
     ctx.close()
     return 0

@@ -169,6 +169,19 @@ mem_status mem_solve(mem_ctx *ctx, float *image_dev_inout, int32_t n_iter,
  * reported a bounded-wait timeout or a CUDA error occurred. */
 mem_status mem_sync(mem_ctx *ctx);
 
+/* The paper's gridded approximation of Eq. (1) (Section 2.4, the steps of
+ * the objective evaluation; Algorithm alg:chi2gpu): each channel's
+ * attenuated image is zero-padded to M = pad * N (image centred), Fourier
+ * transformed on the grid (cuFFT, real to complex, FP32), modulated so that
+ * the phase centre is pixel (N/2, N/2), and the model visibility is
+ * bilinearly interpolated at (u M dx, v M dy).  Not the exact operator the
+ * other entry points evaluate: its error against Eq. (1) falls about as
+ * 1/pad^2 (percent level at pad 2 on smooth images).  image_dev: device,
+ * n_images x N x N float32; vis_dev: device, 2 * Z_total float32 (re, im);
+ * pad in 1..8.  The padded images and spectra (C * M^2 * 4 bytes and about
+ * twice that) stay allocated for the last pad used. */
+mem_status mem_forward_gridded(mem_ctx *ctx, const float *image_dev, int32_t pad, float *vis_dev);
+
 /* Tensor-core tiling.  fwd_kernel selects the forward kernel:
  *   MEM_FWD_STREAM    the split image operand streams through shared memory
  *                     for every 64-visibility tile, in column blocks of

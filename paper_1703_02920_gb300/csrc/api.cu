@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include <cufft.h>
 #include <sys/stat.h>
 
 #include "../../include/libmemsynth.h"
@@ -307,6 +308,14 @@ struct mem_ctx {
     // slice resident in shared memory, N <= 256), pipeline depths
     int fwd_kernel = MEM_FWD_STREAM, fwd_bn = 0, fwd_stages = 4, adj_stages = 3;
     double2* vpart = nullptr;  // resident kernel: slice partials [slice][Z]
+
+    // gridded forward (the paper's FFT + bilinear approximation): padded
+    // images and their half spectra, and the batched cuFFT plan for `grid_pad`
+    int grid_pad = 0;
+    bool grid_plan_ok = false;
+    cufftHandle grid_plan = 0;
+    float* grid_P = nullptr;
+    float2* grid_F = nullptr;
     std::string gpu_name;
 
     // optional per-kernel timing (CUDA events on the context stream)
@@ -402,6 +411,23 @@ mem_status cuda_fail(mem_ctx* c, cudaError_t e, const char* what) {
         cudaError_t e_ = (call);                              \
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
+
+template <typename T>
+mem_status dalloc(mem_ctx* c, T** p, size_t count);
+
+// Release one tracked allocation.
+template <typename T>
+void dfree(mem_ctx* c, T** p, size_t count) {
+    if (!*p) return;
+    for (size_t i = 0; i < c->allocs.size(); ++i)
+        if (c->allocs[i] == (void*)*p) {
+            c->allocs.erase(c->allocs.begin() + i);
+            break;
+        }
+    cudaFree(*p);
+    c->bytes -= std::max<size_t>(count * sizeof(T), 16);
+    *p = nullptr;
+}
 
 template <typename T>
 mem_status dalloc(mem_ctx* c, T** p, size_t count) {
@@ -993,6 +1019,49 @@ mem_status mem_tiling(const mem_ctx* c, mem_tiling_t* out) {
     return MEM_OK;
 }
 
+mem_status mem_forward_gridded(mem_ctx* c, const float* image_dev, int32_t pad, float* vis_dev) {
+    if (!c || !image_dev || (!vis_dev && c->Z > 0)) return fail(c, MEM_EINVAL, "null argument");
+    if (pad < 1 || pad > 8) return fail(c, MEM_EINVAL, "gridded forward: pad must be 1..8 (got %d)", pad);
+    const int M = pad * c->N;
+    const size_t MM = (size_t)M * M, H = (size_t)M * (M / 2 + 1);
+    if (c->grid_pad != pad) {
+        TRY(mem_sync(c));
+        if (c->grid_plan_ok) cufftDestroy(c->grid_plan);
+        c->grid_plan_ok = false;
+        dfree(c, &c->grid_P, (size_t)c->C * (size_t)(c->grid_pad * c->N) * (size_t)(c->grid_pad * c->N));
+        const size_t oldM = (size_t)c->grid_pad * c->N;
+        dfree(c, &c->grid_F, (size_t)c->C * oldM * (oldM / 2 + 1));
+        c->grid_pad = 0;
+        TRY(dalloc(c, &c->grid_P, (size_t)c->C * MM));
+        TRY(dalloc(c, &c->grid_F, (size_t)c->C * H));
+        int n[2] = {M, M};
+        if (cufftPlanMany(&c->grid_plan, 2, n, nullptr, 1, (int)MM, nullptr, 1, (int)H, CUFFT_R2C, c->C) !=
+            CUFFT_SUCCESS)
+            return fail(c, MEM_ECUDA, "cuFFT plan for the gridded forward (M = %d, %d channels)", M, c->C);
+        c->grid_plan_ok = true;
+        c->grid_pad = pad;
+    }
+    if (cufftSetStream(c->grid_plan, c->st) != CUFFT_SUCCESS) return fail(c, MEM_ECUDA, "cuFFT stream");
+    DevData d = c->dd();
+    {
+        KTimer t(c, "grid_pad");
+        launch_grid_pad(d, image_dev, M, c->grid_P, c->st);
+        c->launches++;
+    }
+    TRY(after_launch(c, "gridded forward: padding"));
+    {
+        KTimer t(c, "grid_fft");
+        if (cufftExecR2C(c->grid_plan, (cufftReal*)c->grid_P, (cufftComplex*)c->grid_F) != CUFFT_SUCCESS)
+            return fail(c, MEM_ECUDA, "cuFFT R2C execution");
+    }
+    {
+        KTimer t(c, "grid_interp");
+        launch_grid_interp(d, M, c->grid_F, c->Z, (float2*)vis_dev, c->st);
+        if (c->Z > 0) c->launches++;
+    }
+    return after_launch(c, "gridded forward: interpolation");
+}
+
 mem_status mem_use_graphs(mem_ctx* c, int32_t enable) {
     if (!c) return fail(nullptr, MEM_EINVAL, "null context");
     c->graphs = enable != 0;
@@ -1010,6 +1079,7 @@ void mem_destroy(mem_ctx* c) {
         cudaEventDestroy(k.b);
     }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->grid_plan_ok) cufftDestroy(c->grid_plan);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }

@@ -116,6 +116,10 @@ int fwd_tc_smem_bytes(int BN, int stages);
 // kernel that also applies the forward mode.
 __host__ __device__ inline int fwd_rs_ks(int N) { return N < 128 ? N : 128; }
 int fwd_rs_smem_bytes(int N, int stages);
+// The paper's gridded forward: padding (M = pad N, image centred) and the
+// modulated bilinear interpolation of the batched R2C half spectra.
+void launch_grid_pad(const DevData& d, const float* img, int M, float* P, cudaStream_t st);
+void launch_grid_interp(const DevData& d, int M, const void* F, int64_t z_total, float2* vis, cudaStream_t st);
 int fwd_rs_max_stages(int N);
 void launch_fwd_rs(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
                    const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,

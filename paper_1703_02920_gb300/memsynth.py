@@ -71,7 +71,7 @@ EXPORTS = ["mem_create", "mem_destroy", "mem_last_error", "mem_status_string", "
            "mem_num_vis", "mem_num_images", "mem_forward", "mem_adjoint", "mem_objective_grad",
            "mem_objective_grad_host", "mem_scalars_dev", "mem_solve", "mem_sync", "mem_launch_count",
            "mem_profile", "mem_profile_read", "mem_adjoint_noalloc", "mem_use_graphs", "mem_autotune",
-           "mem_set_tiling", "mem_tiling"]
+           "mem_set_tiling", "mem_tiling", "mem_forward_gridded"]
 
 
 def library_path() -> str:
@@ -131,6 +131,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.mem_set_tiling.restype = ctypes.c_int
     lib.mem_tiling.argtypes = [P, ctypes.POINTER(mem_tiling_t)]
     lib.mem_tiling.restype = ctypes.c_int
+    lib.mem_forward_gridded.argtypes = [P, P, I32, P]
+    lib.mem_forward_gridded.restype = ctypes.c_int
     lib.mem_use_graphs.argtypes = [P, I32]
     lib.mem_use_graphs.restype = ctypes.c_int
     lib.mem_adjoint_noalloc.argtypes = [I32, D, D, I64, P, P, P, P, P, V]
@@ -256,6 +258,11 @@ def mem_tiling(ctx):
     return out.as_tuple()
 
 
+def mem_forward_gridded(ctx, image_dev, pad, vis_dev):
+    """The paper's gridded (FFT + bilinear) approximation of the forward."""
+    _check(load().mem_forward_gridded(ctx, _ptr(image_dev), int(pad), _ptr(vis_dev)), ctx)
+
+
 def mem_use_graphs(ctx, enable: bool):
     _check(load().mem_use_graphs(ctx, int(bool(enable))), ctx)
 
@@ -334,6 +341,13 @@ class Context:
         img = self._img(image)
         out = self.torch.empty((self.Z, 2), dtype=self.torch.float32, device="cuda")
         mem_forward(self.handle, img, out)
+        return out
+
+    def forward_gridded(self, image, pad: int = 2):
+        """The paper's gridded approximation of the model visibilities, (Z, 2)."""
+        img = self._img(image)
+        out = self.torch.empty((self.Z, 2), dtype=self.torch.float32, device="cuda")
+        mem_forward_gridded(self.handle, img, pad, out)
         return out
 
     def adjoint(self, y):
