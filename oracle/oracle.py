@@ -479,6 +479,68 @@ def solve(P: Problem, I0: np.ndarray, n_iter: int, form: str = "factored"):
     return np.stack(imgs), hists
 
 
+def dirty_image(P: Problem, psf: bool = False) -> np.ndarray:
+    """Natural-weights dirty image per channel (Appendix A, Eq. dirty, with the
+    measured visibilities in place of gridded ones), or the PSF (Eq. PSF):
+    I^D(X) = sum_k omega_k Re(V_k exp(+2 pi i U_k . X)), omega_k = w_k / sum_l w_l
+    over the channel's samples; no primary-beam factor.  (C, N, N)."""
+    out = np.zeros((P.C, P.N, P.N))
+    for c in range(P.C):
+        s = P.sl(c)
+        w = P.weights(c)
+        if w.size == 0:
+            continue
+        om = w / np.sum(w)
+        y = om * (np.ones(w.size) if psf else P.vo[s])
+        out[c] = adjoint(P.N, P.dx, P.dy, P.u[s], P.v[s], y.astype(np.complex128))
+    return out
+
+
+BEAM_LOBE = 0.35  # main-lobe pixels: connected to the centre, PSF above this fraction of the peak
+
+
+def beam_fit(psf: np.ndarray, dx: float, dy: float):
+    """Elliptical Gaussian fitted to the PSF's main lobe (Appendix A: BMAJ,
+    BMIN as FWHM, BPA).  Reading: least squares of ln(PSF / PSF0) against the
+    quadratic form -(A x^2 + B x y + C y^2) over the 4-connected region around
+    the centre pixel (N/2, N/2) where PSF > BEAM_LOBE PSF0, with x = (m - N/2) dx,
+    y = (n - N/2) dy.  BPA (degrees, in (-90, 90]) runs from the +y (row) axis
+    towards +x (column).  Returns (BMAJ, BMIN, BPA, beam area in pixels =
+    pi/(4 ln 2) BMAJ BMIN / (dx dy))."""
+    psf = np.asarray(psf, dtype=np.float64)
+    N = psf.shape[0]
+    c = N // 2
+    p0 = psf[c, c]
+    seen = np.zeros_like(psf, dtype=bool)
+    stack, pix = [(c, c)], []
+    seen[c, c] = True
+    while stack:
+        n, m = stack.pop()
+        pix.append((n, m))
+        for dn, dm in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            a, b = n + dn, m + dm
+            if 0 <= a < N and 0 <= b < N and not seen[a, b] and psf[a, b] > BEAM_LOBE * p0:
+                seen[a, b] = True
+                stack.append((a, b))
+    pix = np.array(sorted(pix))
+    x = (pix[:, 1] - c) * dx
+    y = (pix[:, 0] - c) * dy
+    rhs = -np.log(psf[pix[:, 0], pix[:, 1]] / p0)
+    X = np.stack([x * x, x * y, y * y], 1)
+    A, B, C = np.linalg.lstsq(X, rhs, rcond=None)[0]
+    lam, vec = np.linalg.eigh(np.array([[A, B / 2], [B / 2, C]]))
+    if lam[0] <= 0:
+        raise ValueError("the PSF main lobe is not a peak")
+    bmaj, bmin = 2 * math.sqrt(math.log(2) / lam[0]), 2 * math.sqrt(math.log(2) / lam[1])
+    ex, ey = vec[0, 0], vec[1, 0]  # major axis (smallest curvature)
+    bpa = math.degrees(math.atan2(ex, ey))
+    if bpa <= -90:
+        bpa += 180
+    if bpa > 90:
+        bpa -= 180
+    return bmaj, bmin, bpa, math.pi / (4 * math.log(2)) * bmaj * bmin / (dx * dy)
+
+
 def kkt_residual(I: np.ndarray, g: np.ndarray, G: float) -> float:
     """|| I - max(I - g, G) ||: zero exactly at a point satisfying the bound-
     constrained first-order conditions."""

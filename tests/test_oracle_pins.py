@@ -408,3 +408,47 @@ def test_gridded_forward_is_hermitian_and_converges_with_padding(oracle_mod):
         errs.append(np.max(np.abs(g - d)) / np.max(np.abs(d)))
     assert errs[0] > errs[1] > errs[2] > errs[3], errs
     assert errs[3] < 0.05 * errs[0], errs
+
+
+# ---------------------------------------------------------------------------
+# dirty image, PSF and beam (Appendix A)
+# ---------------------------------------------------------------------------
+def test_psf_peaks_at_one_and_point_source_dirty_image_is_shifted_psf(oracle_mod):
+    """sum omega = 1 puts the PSF's peak (1) at the phase centre.  A noiseless
+    point source of flux f at pixel (n0, m0) has V_k = f exp(-2 pi i U_k . X0),
+    so by the shift theorem its dirty image is f PSF(X - X0)."""
+    ds = S.random_problem(32, 300, 91)
+    N, c = ds.N, ds.N // 2
+    f, n0, m0 = 0.7, 19, 11
+    x0, y0 = (m0 - c) * ds.dx, (n0 - c) * ds.dy
+    ds.vo = f * np.exp(-2j * np.pi * (ds.u * x0 + ds.v * y0))
+    P = oracle_mod.Problem.from_dataset(ds)
+    psf = oracle_mod.dirty_image(P, psf=True)[0]
+    assert psf[c, c] == pytest.approx(1.0, abs=1e-12)
+    assert np.max(psf) == pytest.approx(1.0, abs=1e-12)
+    dirty = oracle_mod.dirty_image(P)[0]
+    dn, dm = n0 - c, m0 - c
+    # dirty[n, m] = f psf[n - dn, m - dm] wherever both indices are on the grid
+    sub = dirty[max(dn, 0):N + min(dn, 0), max(dm, 0):N + min(dm, 0)]
+    ref = f * psf[max(-dn, 0):N + min(-dn, 0), max(-dm, 0):N + min(-dm, 0)]
+    assert np.max(np.abs(sub - ref)) <= 1e-12
+    assert np.unravel_index(np.argmax(dirty), dirty.shape) == (n0, m0)
+
+
+def test_beam_fit_recovers_an_elliptical_gaussian(oracle_mod):
+    N = 64
+    dx, dy = 0.05e-6, 0.07e-6
+    for bmaj, bmin, bpa in [(9e-7, 5e-7, 30.0), (1.2e-6, 1.2e-6 * 0.999, -75.0), (8e-7, 3e-7, 90.0)]:
+        n, m = np.mgrid[0:N, 0:N]
+        x, y = (m - N // 2) * dx, (n - N // 2) * dy
+        t = np.radians(bpa)
+        a = x * np.sin(t) + y * np.cos(t)   # along the major axis (from +y towards +x)
+        b = x * np.cos(t) - y * np.sin(t)
+        s2 = 1 / (8 * np.log(2))
+        psf = np.exp(-(a ** 2 / (s2 * bmaj ** 2) + b ** 2 / (s2 * bmin ** 2)) / 2)
+        got = oracle_mod.beam_fit(psf, dx, dy)
+        assert got[0] == pytest.approx(bmaj, rel=1e-9)
+        assert got[1] == pytest.approx(bmin, rel=1e-9)
+        if bmaj / bmin > 1.01:
+            assert (got[2] - bpa + 90) % 180 - 90 == pytest.approx(0.0, abs=1e-6)
+        assert got[3] == pytest.approx(np.pi / (4 * np.log(2)) * bmaj * bmin / (dx * dy), rel=1e-9)
