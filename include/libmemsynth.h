@@ -182,6 +182,26 @@ mem_status mem_sync(mem_ctx *ctx);
  * twice that) stay allocated for the last pad used. */
 mem_status mem_forward_gridded(mem_ctx *ctx, const float *image_dev, int32_t pad, float *vis_dev);
 
+/* Natural-weights dirty image per channel (Appendix A, Eq. dirty, with the
+ * measured visibilities in place of gridded ones) or, with psf != 0, the
+ * PSF (Eq. PSF):
+ *   I^D[c](X) = sum_k omega_k Re(V_k exp(+2 pi i U_k . X)),
+ *   omega_k = (1/sigma_k^2) / sum over the channel's samples of 1/sigma^2,
+ * with V_k = 1 for the PSF; no primary-beam factor.  Runs the context's
+ * adjoint in its precision form.  out_dev: device, C x N x N float32. */
+mem_status mem_dirty_image(mem_ctx *ctx, int32_t psf, float *out_dev);
+
+/* Elliptical Gaussian fitted to a PSF's main lobe (Appendix A: BMAJ, BMIN,
+ * BPA).  Host function, no GPU.  The main lobe is the 4-connected region
+ * around the centre pixel (n/2, n/2) where the PSF exceeds 0.35 of its value
+ * there; ln(PSF / PSF0) is fitted by least squares to -(A x^2 + B x y + C y^2)
+ * with x = (m - n/2) dx, y = (row - n/2) dy (radians).  out4 (host): BMAJ and
+ * BMIN (FWHM, radians), BPA (degrees in (-90, 90], from the +y (row) axis
+ * towards +x (column)), and the beam area in pixels, pi/(4 ln 2) BMAJ BMIN /
+ * (dx dy), which converts Jy/beam to Jy/pixel.  MEM_ENUMERIC when the lobe is
+ * not a peak. */
+mem_status mem_beam_fit(const float *psf_host, int32_t n, double dx, double dy, double *out4);
+
 /* Tensor-core tiling.  fwd_kernel selects the forward kernel:
  *   MEM_FWD_STREAM    the split image operand streams through shared memory
  *                     for every 64-visibility tile, in column blocks of

@@ -311,6 +311,8 @@ struct mem_ctx {
 
     // gridded forward (the paper's FFT + bilinear approximation): padded
     // images and their half spectra, and the batched cuFFT plan for `grid_pad`
+    std::vector<double> wsum_h;   // per-channel sum of weights (natural-weights dirty image)
+    double* wsum = nullptr;
     int grid_pad = 0;
     bool grid_plan_ok = false;
     cufftHandle grid_plan = 0;
@@ -1062,6 +1064,96 @@ mem_status mem_forward_gridded(mem_ctx* c, const float* image_dev, int32_t pad, 
     return after_launch(c, "gridded forward: interpolation");
 }
 
+mem_status mem_dirty_image(mem_ctx* c, int32_t psf, float* out_dev) {
+    if (!c || !out_dev) return fail(c, MEM_EINVAL, "null argument");
+    TRY(ensure_buffers(c));
+    if (!c->wsum) {
+        TRY(dalloc(c, &c->wsum, (size_t)c->C));
+        CK(cudaMemcpyAsync(c->wsum, c->wsum_h.data(), c->C * sizeof(double), cudaMemcpyHostToDevice, c->st),
+           "weight sums");
+    }
+    DevData d = c->dd();
+    launch_dirty_y(d, c->wsum, psf ? 1 : 0, c->Z, c->y32, c->prec == MEM_PREC_FP64_DIRECT ? c->y64 : nullptr,
+                   c->st);
+    if (c->Z > 0) c->launches++;
+    TRY(after_launch(c, "dirty image weights"));
+    int ks = 1;
+    TRY(run_adjoint(c, &ks));
+    launch_dirty_out(d, c->gsum, ks, out_dev, c->st);
+    c->launches++;
+    return after_launch(c, "dirty image");
+}
+
+mem_status mem_beam_fit(const float* psf, int32_t n, double dx, double dy, double* out4) {
+    if (!psf || !out4 || n < 3 || !(dx > 0) || !(dy > 0)) return MEM_EINVAL;
+    const int c0 = n / 2;
+    const double p0 = psf[(int64_t)c0 * n + c0];
+    if (!(p0 > 0)) return MEM_EINVAL;
+    // main lobe: 4-connected to the centre, above BEAM_LOBE of the peak
+    const double lobe = 0.35;
+    std::vector<char> seen((size_t)n * n, 0);
+    std::vector<int> stack{c0 * n + c0};
+    seen[(size_t)c0 * n + c0] = 1;
+    double S[3][3] = {{0}}, R[3] = {0};
+    while (!stack.empty()) {
+        const int q = stack.back();
+        stack.pop_back();
+        const int a = q / n, b = q % n;
+        const double x = (b - c0) * dx, y = (a - c0) * dy;
+        const double f[3] = {x * x, x * y, y * y};
+        const double r = -std::log(psf[q] / p0);
+        for (int i = 0; i < 3; ++i) {
+            R[i] += f[i] * r;
+            for (int j = 0; j < 3; ++j) S[i][j] += f[i] * f[j];
+        }
+        const int nb[4][2] = {{a + 1, b}, {a - 1, b}, {a, b + 1}, {a, b - 1}};
+        for (auto& t : nb)
+            if (t[0] >= 0 && t[0] < n && t[1] >= 0 && t[1] < n && !seen[(size_t)t[0] * n + t[1]] &&
+                psf[(size_t)t[0] * n + t[1]] > lobe * p0) {
+                seen[(size_t)t[0] * n + t[1]] = 1;
+                stack.push_back(t[0] * n + t[1]);
+            }
+    }
+    // normal equations S (A, B, C) = R by Cramer's rule
+    auto det3 = [](double m[3][3]) {
+        return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+               m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+    };
+    const double D = det3(S);
+    if (!(std::fabs(D) > 0)) return MEM_ENUMERIC;
+    double abc[3];
+    for (int k = 0; k < 3; ++k) {
+        double T[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) T[i][j] = (j == k) ? R[i] : S[i][j];
+        abc[k] = det3(T) / D;
+    }
+    // quadratic form [[A, B/2], [B/2, C]]: eigenvalues and the major axis
+    const double A = abc[0], B2 = abc[1] / 2, C = abc[2];
+    const double tr = A + C, disc = std::sqrt(std::max(0.0, (A - C) * (A - C) / 4 + B2 * B2));
+    const double l_min = tr / 2 - disc, l_max = tr / 2 + disc;
+    if (!(l_min > 0)) return MEM_ENUMERIC;
+    const double bmaj = 2 * std::sqrt(std::log(2.0) / l_min), bmin = 2 * std::sqrt(std::log(2.0) / l_max);
+    // eigenvector of l_min: (B/2, l_min - A) or (l_min - C, B/2)
+    double ex = B2, ey = l_min - A;
+    if (std::fabs(ex) + std::fabs(ey) < 1e-300 * (std::fabs(A) + std::fabs(C))) {
+        ex = l_min - C;
+        ey = B2;
+    }
+    if (std::fabs(ex) + std::fabs(ey) == 0) {  // circular beam
+        ex = 0;
+        ey = 1;
+    }
+    double bpa = std::atan2(ex, ey) * 180.0 / M_PI;
+    if (bpa <= -90) bpa += 180;
+    if (bpa > 90) bpa -= 180;
+    out4[0] = bmaj;
+    out4[1] = bmin;
+    out4[2] = bpa;
+    out4[3] = M_PI / (4 * std::log(2.0)) * bmaj * bmin / (dx * dy);
+    return MEM_OK;
+}
+
 mem_status mem_use_graphs(mem_ctx* c, int32_t enable) {
     if (!c) return fail(nullptr, MEM_EINVAL, "null context");
     c->graphs = enable != 0;
@@ -1169,6 +1261,9 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
     }
     std::vector<double> wh((size_t)Z);
     for (int64_t k = 0; k < Z; ++k) wh[k] = 1.0 / (sigma[k] * sigma[k]);
+    c->wsum_h.assign((size_t)C, 0.0);
+    for (int ch = 0; ch < C; ++ch)
+        for (int64_t k = c->off[ch]; k < c->off[ch + 1]; ++k) c->wsum_h[ch] += wh[k];
     auto cpy = [&](void* dst, const void* src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->st) : cudaSuccess;
     };

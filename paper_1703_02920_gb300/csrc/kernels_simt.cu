@@ -679,3 +679,51 @@ void launch_f64_to_f32(int64_t n, const double* in, float* out, cudaStream_t st)
 }
 
 }  // namespace msk
+
+namespace msk {
+
+// ---------------------------------------------------------------------------
+// Dirty image and PSF (Appendix A, Eq. dirty and Eq. PSF): the adjoint of
+// y_k = omega_k V_k (or omega_k), omega_k = w_k / (sum of w over the channel);
+// the sum of the adjoint's splits per channel, without the primary beam.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_dirty_y(DevData d, const double* __restrict__ wsum, int psf,
+                                                 int64_t z_total, float2* __restrict__ y32,
+                                                 double2* __restrict__ y64) {
+    const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (j >= z_total) return;
+    int lo = 0, hi = d.C;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (d.off[mid] <= j) lo = mid;
+        else hi = mid;
+    }
+    const double om = d.w[j] / wsum[lo];
+    const double2 v = psf ? make_double2(1.0, 0.0) : d.vo[j];
+    y32[j] = make_float2((float)(om * v.x), (float)(om * v.y));
+    if (y64) y64[j] = make_double2(om * v.x, om * v.y);
+}
+
+__global__ void __launch_bounds__(256) k_dirty_out(DevData d, const double* __restrict__ gsum, int ks,
+                                                   float* __restrict__ out) {
+    const int64_t NN = (int64_t)d.N * d.N;
+    const int c = blockIdx.y;
+    const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (p >= NN) return;
+    double s = 0.0;
+    for (int k = 0; k < ks; ++k) s += gsum[((int64_t)k * d.C + c) * NN + p];
+    out[(int64_t)c * NN + p] = (float)s;
+}
+
+void launch_dirty_y(const DevData& d, const double* wsum, int psf, int64_t z_total, float2* y32, double2* y64,
+                    cudaStream_t st) {
+    if (z_total <= 0) return;
+    k_dirty_y<<<(unsigned)((z_total + 255) / 256), 256, 0, st>>>(d, wsum, psf, z_total, y32, y64);
+}
+
+void launch_dirty_out(const DevData& d, const double* gsum, int ks, float* out, cudaStream_t st) {
+    dim3 grid(prep_blocks(d.N), d.C);
+    k_dirty_out<<<grid, 256, 0, st>>>(d, gsum, ks, out);
+}
+
+}  // namespace msk

@@ -71,7 +71,8 @@ EXPORTS = ["mem_create", "mem_destroy", "mem_last_error", "mem_status_string", "
            "mem_num_vis", "mem_num_images", "mem_forward", "mem_adjoint", "mem_objective_grad",
            "mem_objective_grad_host", "mem_scalars_dev", "mem_solve", "mem_sync", "mem_launch_count",
            "mem_profile", "mem_profile_read", "mem_adjoint_noalloc", "mem_use_graphs", "mem_autotune",
-           "mem_set_tiling", "mem_tiling", "mem_forward_gridded"]
+           "mem_set_tiling", "mem_tiling", "mem_forward_gridded",
+           "mem_dirty_image", "mem_beam_fit"]
 
 
 def library_path() -> str:
@@ -133,6 +134,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.mem_tiling.restype = ctypes.c_int
     lib.mem_forward_gridded.argtypes = [P, P, I32, P]
     lib.mem_forward_gridded.restype = ctypes.c_int
+    lib.mem_dirty_image.argtypes = [P, I32, P]
+    lib.mem_dirty_image.restype = ctypes.c_int
+    lib.mem_beam_fit.argtypes = [P, I32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.mem_beam_fit.restype = ctypes.c_int
     lib.mem_use_graphs.argtypes = [P, I32]
     lib.mem_use_graphs.restype = ctypes.c_int
     lib.mem_adjoint_noalloc.argtypes = [I32, D, D, I64, P, P, P, P, P, V]
@@ -263,6 +268,19 @@ def mem_forward_gridded(ctx, image_dev, pad, vis_dev):
     _check(load().mem_forward_gridded(ctx, _ptr(image_dev), int(pad), _ptr(vis_dev)), ctx)
 
 
+def mem_dirty_image(ctx, psf: bool, out_dev):
+    _check(load().mem_dirty_image(ctx, int(bool(psf)), _ptr(out_dev)), ctx)
+
+
+def mem_beam_fit(psf, dx: float, dy: float):
+    """(BMAJ, BMIN, BPA, beam area in pixels) of a host PSF image (n x n float32)."""
+    import numpy as np
+    a = np.ascontiguousarray(psf, dtype=np.float32)
+    out = (ctypes.c_double * 4)()
+    _check(load().mem_beam_fit(a.ctypes.data, int(a.shape[0]), float(dx), float(dy), out), None)
+    return tuple(out)
+
+
 def mem_use_graphs(ctx, enable: bool):
     _check(load().mem_use_graphs(ctx, int(bool(enable))), ctx)
 
@@ -348,6 +366,12 @@ class Context:
         img = self._img(image)
         out = self.torch.empty((self.Z, 2), dtype=self.torch.float32, device="cuda")
         mem_forward_gridded(self.handle, img, pad, out)
+        return out
+
+    def dirty_image(self, psf: bool = False):
+        """Natural-weights dirty image (or PSF) per channel, (C, N, N) float32."""
+        out = self.torch.empty((self.C, self.N, self.N), dtype=self.torch.float32, device="cuda")
+        mem_dirty_image(self.handle, psf, out)
         return out
 
     def adjoint(self, y):
