@@ -191,6 +191,20 @@ mem_status mem_forward_gridded(mem_ctx *ctx, const float *image_dev, int32_t pad
  * adjoint in its precision form.  out_dev: device, C x N x N float32. */
 mem_status mem_dirty_image(mem_ctx *ctx, int32_t psf, float *out_dev);
 
+/* Mosaics (Section 2.4: one attenuation image per pointing, centred on its
+ * field).  A pointing whose phase-tracking centre lies at (x_p, y_p)
+ * (radians, relative to the image's phase centre, pixel (N/2, N/2)) measures
+ * V_p = exp(+2 pi i (u x_p + v y_p)) F(A_p I).  The factor has unit modulus, so
+ * its chi^2 equals that of the visibilities rotated to the image's phase
+ * centre, vis *= exp(-2 pi i (u x_p + v y_p)).  This host function applies
+ * that rotation in place (FP64, the phase reduced modulo one turn before the
+ * sine and cosine).  With each pointing's rotated data and its beam (centred
+ * on the pointing) as one channel of a MEM_IMAGE_SHARED context, the
+ * context's objective, gradient and solve are the mosaic's.  u, v (n_vis,
+ * wavelengths) and vis (2 * n_vis, interleaved re, im) on the host. */
+mem_status mem_phase_rotate(int64_t n_vis, const double *u, const double *v, double x_p, double y_p,
+                            double *vis_inout);
+
 /* Elliptical Gaussian fitted to a PSF's main lobe (Appendix A: BMAJ, BMIN,
  * BPA).  Host function, no GPU.  The main lobe is the 4-connected region
  * around the centre pixel (n/2, n/2) where the PSF exceeds 0.35 of its value

@@ -479,6 +479,17 @@ def solve(P: Problem, I0: np.ndarray, n_iter: int, form: str = "factored"):
     return np.stack(imgs), hists
 
 
+def mosaic_forward(N: int, dx: float, dy: float, u, v, A_p, I, x_p: float, y_p: float) -> np.ndarray:
+    """One pointing of a mosaic (Section 2.4: an attenuation image per pointing,
+    centred on its field): the sky I seen through the pointing's primary beam
+    A_p (already centred at the pointing, an N x N image on the same grid) with
+    the phase referenced to the pointing centre (x_p, y_p):
+    V_k = sum_{n,m} A_p[n,m] I[n,m] exp(-2 pi i (u_k (x_m - x_p) + v_k (y_n - y_p)))."""
+    u, v = _f64(u), _f64(v)
+    B = _f64(A_p).reshape(N, N) * _f64(I).reshape(N, N)
+    return forward(N, dx, dy, u, v, B) * np.exp(2j * np.pi * (u * x_p + v * y_p))
+
+
 def dirty_image(P: Problem, psf: bool = False) -> np.ndarray:
     """Natural-weights dirty image per channel (Appendix A, Eq. dirty, with the
     measured visibilities in place of gridded ones), or the PSF (Eq. PSF):

@@ -1084,6 +1084,20 @@ mem_status mem_dirty_image(mem_ctx* c, int32_t psf, float* out_dev) {
     return after_launch(c, "dirty image");
 }
 
+mem_status mem_phase_rotate(int64_t n_vis, const double* u, const double* v, double x_p, double y_p,
+                            double* vis) {
+    if (n_vis < 0 || (n_vis > 0 && (!u || !v || !vis))) return MEM_EINVAL;
+    for (int64_t k = 0; k < n_vis; ++k) {
+        double t = u[k] * x_p + v[k] * y_p;  // turns
+        t -= std::floor(t);
+        const double cr = std::cos(2 * M_PI * t), sr = -std::sin(2 * M_PI * t);
+        const double re = vis[2 * k], im = vis[2 * k + 1];
+        vis[2 * k] = re * cr - im * sr;
+        vis[2 * k + 1] = re * sr + im * cr;
+    }
+    return MEM_OK;
+}
+
 mem_status mem_beam_fit(const float* psf, int32_t n, double dx, double dy, double* out4) {
     if (!psf || !out4 || n < 3 || !(dx > 0) || !(dy > 0)) return MEM_EINVAL;
     const int c0 = n / 2;

@@ -72,7 +72,7 @@ EXPORTS = ["mem_create", "mem_destroy", "mem_last_error", "mem_status_string", "
            "mem_objective_grad_host", "mem_scalars_dev", "mem_solve", "mem_sync", "mem_launch_count",
            "mem_profile", "mem_profile_read", "mem_adjoint_noalloc", "mem_use_graphs", "mem_autotune",
            "mem_set_tiling", "mem_tiling", "mem_forward_gridded",
-           "mem_dirty_image", "mem_beam_fit"]
+           "mem_dirty_image", "mem_beam_fit", "mem_phase_rotate"]
 
 
 def library_path() -> str:
@@ -138,6 +138,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.mem_dirty_image.restype = ctypes.c_int
     lib.mem_beam_fit.argtypes = [P, I32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     lib.mem_beam_fit.restype = ctypes.c_int
+    lib.mem_phase_rotate.argtypes = [ctypes.c_int64, P, P, ctypes.c_double, ctypes.c_double, P]
+    lib.mem_phase_rotate.restype = ctypes.c_int
     lib.mem_use_graphs.argtypes = [P, I32]
     lib.mem_use_graphs.restype = ctypes.c_int
     lib.mem_adjoint_noalloc.argtypes = [I32, D, D, I64, P, P, P, P, P, V]
@@ -279,6 +281,17 @@ def mem_beam_fit(psf, dx: float, dy: float):
     out = (ctypes.c_double * 4)()
     _check(load().mem_beam_fit(a.ctypes.data, int(a.shape[0]), float(dx), float(dy), out), None)
     return tuple(out)
+
+
+def mem_phase_rotate(u, v, vis, x_p: float, y_p: float):
+    """Visibilities (complex array) rotated from a pointing's phase centre
+    (x_p, y_p) to the image's: returns a new complex128 array."""
+    import numpy as np
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    buf = np.ascontiguousarray(np.stack([np.real(vis), np.imag(vis)], 1), dtype=np.float64)
+    _check(load().mem_phase_rotate(u.size, u.ctypes.data, v.ctypes.data, float(x_p), float(y_p), buf.ctypes.data), None)
+    return buf[:, 0] + 1j * buf[:, 1]
 
 
 def mem_use_graphs(ctx, enable: bool):

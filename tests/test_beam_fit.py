@@ -36,3 +36,17 @@ def test_beam_fit_matches_oracle_on_gaussian_and_on_a_psf(lib, oracle_mod):
 def test_beam_fit_rejects_bad_input(lib):
     with pytest.raises(lib.MemError):
         lib.mem_beam_fit(np.zeros((16, 16), np.float32), 1e-6, 1e-6)
+
+
+def test_phase_rotation_is_the_unit_modulus_factor(lib):
+    """mem_phase_rotate multiplies by exp(-2 pi i (u x_p + v y_p)); a rotation
+    and its inverse return the data."""
+    rng = np.random.default_rng(7)
+    u, v = rng.uniform(-2e6, 2e6, 300), rng.uniform(-2e6, 2e6, 300)
+    V = rng.standard_normal(300) + 1j * rng.standard_normal(300)
+    xp, yp = 3.3e-6, -1.7e-6
+    got = lib.mem_phase_rotate(u, v, V, xp, yp)
+    ref = V * np.exp(-2j * np.pi * (u * xp + v * yp))
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(V))
+    back = lib.mem_phase_rotate(u, v, got, -xp, -yp)
+    assert np.max(np.abs(back - V)) <= 1e-12 * np.max(np.abs(V))

@@ -452,3 +452,25 @@ def test_beam_fit_recovers_an_elliptical_gaussian(oracle_mod):
         if bmaj / bmin > 1.01:
             assert (got[2] - bpa + 90) % 180 - 90 == pytest.approx(0.0, abs=1e-6)
         assert got[3] == pytest.approx(np.pi / (4 * np.log(2)) * bmaj * bmin / (dx * dy), rel=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# mosaic pointing (Section 2.4: one attenuation image per pointing)
+# ---------------------------------------------------------------------------
+def test_mosaic_pointing_of_a_point_source_is_its_closed_form(oracle_mod):
+    """A point source of flux f at X_s seen by a pointing centred at X_p:
+    V = f A_p(X_s) exp(-2 pi i U . (X_s - X_p))."""
+    N, dx = 48, 1e-6
+    c = N // 2
+    rng = np.random.default_rng(6)
+    u, v = rng.uniform(-4e5, 4e5, 50), rng.uniform(-4e5, 4e5, 50)
+    ns, ms_ = 30, 17
+    I = np.zeros((N, N))
+    I[ns, ms_] = 0.8
+    xp, yp = 7 * dx, -5 * dx
+    n, m = np.mgrid[0:N, 0:N]
+    A = np.exp(-(((m - c) * dx - xp) ** 2 + ((n - c) * dx - yp) ** 2) / (2 * (12 * dx) ** 2))
+    V = oracle_mod.mosaic_forward(N, dx, dx, u, v, A, I, xp, yp)
+    xs, ys = (ms_ - c) * dx, (ns - c) * dx
+    ref = 0.8 * A[ns, ms_] * np.exp(-2j * np.pi * (u * (xs - xp) + v * (ys - yp)))
+    assert np.max(np.abs(V - ref)) <= 1e-12
