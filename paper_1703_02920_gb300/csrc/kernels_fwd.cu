@@ -199,10 +199,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             for (int mb = 0; mb < n_mb && ok; ++mb) {
                 for (int ks = 0; ks < nk; ++ks, ++sc) {
                     const int s = sc % F2_STAGES;
-                    ok = __all_sync(0xffffffffu, mbar_wait(&S.empty[s], ((sc / F2_STAGES) & 1) ^ 1, spin,
-                                                           abort, status, 64));
-                    if (!ok) break;
-                    unsigned char* A = smem + s * stage_bytes;
+                    // the table values need no ring slot: compute them, then wait
                     uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
                     if (valid) {
                         const int n0 = ks * TC_BK + g * 8;
@@ -219,6 +216,10 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                         split16x2<F16>(z[4].y, z[5].y, ih.z, il.z);
                         split16x2<F16>(z[6].y, z[7].y, ih.w, il.w);
                     }
+                    ok = __all_sync(0xffffffffu, mbar_wait(&S.empty[s], ((sc / F2_STAGES) & 1) ^ 1, spin,
+                                                           abort, status, 64));
+                    if (!ok) break;
+                    unsigned char* A = smem + s * stage_bytes;
                     *(uint4*)(A + off) = rh;
                     *(uint4*)(A + off + 256) = ih;
                     *(uint4*)(A + F2_APLANE + off) = rl;

@@ -200,10 +200,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             for (int pass = 0; pass < 2 && ok; ++pass) {
                 for (int ks = 0; ks < nks; ++ks, ++sc) {
                     const int s = sc % STAGES;
-                    ok = __all_sync(0xffffffffu, mbar_wait(&S.empty[s], ((sc / STAGES) & 1) ^ 1, spin, abort,
-                                                           status, 64));
-                    if (!ok) break;
-                    unsigned char* A = sA + s * RS_ABYTES;
+                    // the table values need no ring slot: compute them, then wait
                     uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
                     if (valid) {
                         const int n0 = slice * KS + ks * TC_BK + g * 8;
@@ -220,6 +217,10 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                         split16x2<F16>(z[4].y, z[5].y, ih.z, il.z);
                         split16x2<F16>(z[6].y, z[7].y, ih.w, il.w);
                     }
+                    ok = __all_sync(0xffffffffu, mbar_wait(&S.empty[s], ((sc / STAGES) & 1) ^ 1, spin, abort,
+                                                           status, 64));
+                    if (!ok) break;
+                    unsigned char* A = sA + s * RS_ABYTES;
                     *(uint4*)(A + off) = rh;
                     *(uint4*)(A + off + 256) = ih;
                     if (pass == 0) {  // the hi*hi pass reads the hi plane only

@@ -262,13 +262,9 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                 const cf2 yv = {ny.x * ysc, ny.y * ysc};
                 const bool valid = (int64_t)ks * TCA_BK + jj < un.count;
                 fetch(ks + 1, na, nb, ny);
-                ok = __all_sync(0xffffffffu, mbar_wait(&S.empty[s], ((sc / ADJ_STAGES) & 1) ^ 1, spin,
-                                                       abort, status, 64));
-                if (!ok) break;
-                unsigned char* A = smem + s * stage_bytes;
-                unsigned char* B = A + 4 * a_plane;
                 // rotation steps exp(-i 2 pi q c), q = 0..7, by powers of one SFU
-                // value: c = b for the Ey side, a for the P side
+                // value: c = b for the Ey side, a for the P side (computed before
+                // the wait for the ring slot, which they do not need)
                 cf2 st[8];
                 st[0] = {1.f, 0.f};
                 st[1] = cis_neg(ey_side ? pb : pa);
@@ -278,6 +274,11 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                 st[5] = cmul(st[4], st[1]);
                 st[6] = cmul(st[4], st[2]);
                 st[7] = cmul(st[4], st[3]);
+                ok = __all_sync(0xffffffffu, mbar_wait(&S.empty[s], ((sc / ADJ_STAGES) & 1) ^ 1, spin,
+                                                       abort, status, 64));
+                if (!ok) break;
+                unsigned char* A = smem + s * stage_bytes;
+                unsigned char* B = A + 4 * a_plane;
                 for (int it2 = side_grp; it2 < (ey_side ? ngA : ngB); it2 += n_groups / 2) {
                     const int item = ey_side ? it2 : ngA + it2;
                     uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
