@@ -285,7 +285,7 @@ struct mem_ctx {
     float *cmax = nullptr, *cscale = nullptr;   // FP16X3 operand scales per channel
     double* col_psum = nullptr;                 // column-mean partial sums
     float* col_pmax = nullptr;
-    float *yscale = nullptr, *ymax_part = nullptr;  // FP16X3 scale of the adjoint input
+    float *ymax = nullptr, *ymax_part = nullptr;  // FP16X3: max |y| (adjoint operand scale), partials
     float* partial = nullptr;  // adjoint unit partials (FP32, one BLK x BLK block each)
     int* dstatus = nullptr;
     float* stage = nullptr;  // host-call staging (image, gradient)
@@ -553,7 +553,11 @@ mem_status ensure_buffers(mem_ctx* c) {
     TRY(dalloc(c, &c->chi_part, (size_t)4 * std::max(std::max(c->n_tiles, c->n_tiles_tc), 1)));
     TRY(dalloc(c, &c->ent_part, (size_t)c->n_images * prep_blocks(c->N)));
     TRY(dalloc(c, &c->scal, (size_t)3 + 3 * c->n_images));
-    TRY(dalloc(c, &c->img_tmp, (size_t)scalars_tmp_doubles(c->n_images)));
+    if (!c->img_tmp) {  // holds the scalar reduction's completion counter, which starts at zero
+        TRY(dalloc(c, &c->img_tmp, (size_t)scalars_tmp_doubles(c->n_images)));
+        CK(cudaMemsetAsync(c->img_tmp, 0, scalars_tmp_doubles(c->n_images) * sizeof(double), c->st),
+           "scalar reduction buffer");
+    }
     TRY(dalloc(c, &c->y32, (size_t)std::max<int64_t>(c->Z, 1)));
     if (c->prec == MEM_PREC_FP64_DIRECT) {
         TRY(dalloc(c, &c->y64, (size_t)std::max<int64_t>(c->Z, 1)));
@@ -567,7 +571,7 @@ mem_status ensure_buffers(mem_ctx* c) {
         TRY(dalloc(c, &c->col_psum, (size_t)colmean_tmp_count(c->N, c->C)));
         TRY(dalloc(c, &c->col_pmax, (size_t)colmean_tmp_count(c->N, c->C)));
         TRY(dalloc(c, &c->cscale, (size_t)c->C));
-        TRY(dalloc(c, &c->yscale, (size_t)1));
+        TRY(dalloc(c, &c->ymax, (size_t)1));
         TRY(dalloc(c, &c->ymax_part, (size_t)256));
         const int BLK = tca_blk(c->N);
         TRY(dalloc(c, &c->partial, std::max<size_t>(c->units_h.size(), 1) * BLK * BLK));
@@ -613,15 +617,18 @@ mem_status run_forward(mem_ctx* c, const ImgSrc& src, int mode, bool entropy, vo
     }
     c->launches++;
     TRY(after_launch(c, "prep kernel"));
+    // FP16X3: the weighted residual's maximum for the adjoint's operand scale
+    float* ymax = (tc && f16 && mode == FWD_RESID) ? c->ymax : nullptr;
+    if (ymax) CK(cudaMemsetAsync(ymax, 0, sizeof(float), c->st), "residual maximum");
     if (tc && c->fwd_kernel == MEM_FWD_RESIDENT) {
         KTimer t(c, "fwd_rs");
         launch_fwd_rs(d, f16, c->tiles_tc, c->n_tiles_tc, c->planes, c->cmean, c->cscale, mode, (float2*)yout,
-                      c->chi_part, c->vpart, c->Z, c->num_sms, c->spin, c->dstatus, c->st);
+                      c->chi_part, ymax, c->vpart, c->Z, c->num_sms, c->spin, c->dstatus, c->st);
         if (c->n_tiles_tc > 0) c->launches++;  // + the slice combination
     } else if (tc) {
         KTimer t(c, "fwd_tc");
         launch_fwd_tc(d, f16, c->tiles_tc, c->n_tiles_tc, c->planes, c->cmean, c->cscale, mode, (float2*)yout,
-                      c->chi_part, c->num_sms, c->spin, c->dstatus, c->st);
+                      c->chi_part, ymax, c->num_sms, c->spin, c->dstatus, c->st);
     } else {
         KTimer t(c, c->prec == MEM_PREC_FP64_DIRECT ? "fwd_direct_f64" : "fwd_direct_f32");
         launch_fwd_direct(d, c->prec == MEM_PREC_FP64_DIRECT, c->tiles, c->n_tiles, bbuf(c), mode, yout,
@@ -633,31 +640,33 @@ mem_status run_forward(mem_ctx* c, const ImgSrc& src, int mode, bool entropy, vo
         KTimer t(c, "scalars");
         launch_scalars(d, tc ? c->tile_off_tc : c->tile_off, c->chi_part, c->ent_part, entropy ? 1 : 0,
                        c->scal, c->img_tmp, c->st);
-        c->launches += 2;
+        c->launches++;
         TRY(after_launch(c, "scalar reduction"));
     }
     return MEM_OK;
 }
 
 // adjoint of y (already in y32 / y64) into gsum; returns ks used.
-mem_status run_adjoint(mem_ctx* c, int* ks_out) {
+// ymax_ready: the FP16X3 operand scale's maximum was written by the RESID
+// forward that produced y32.
+mem_status run_adjoint(mem_ctx* c, int* ks_out, bool ymax_ready = false) {
     DevData d = c->dd();
     if (is_tc(c->prec)) {
         const int f16 = c->prec == MEM_PREC_FP16X3;
-        if (f16) {
-            KTimer t(c, "yscale");
-            launch_absmax_scale(2 * c->Z, (const float*)c->y32, c->ymax_part, c->yscale, c->st);
+        if (f16 && !ymax_ready) {
+            KTimer t(c, "ymax");
+            launch_absmax(2 * c->Z, (const float*)c->y32, c->ymax_part, c->ymax, c->st);
             c->launches += 2;
         }
         if (c->adj_ctas > 0) {
             KTimer t(c, "adj_tc");
-            launch_adj_tc(d, f16, c->units, c->cta_off, c->adj_ctas, c->y32, c->yscale, c->partial, c->spin,
+            launch_adj_tc(d, f16, c->units, c->cta_off, c->adj_ctas, c->y32, c->ymax, c->partial, c->spin,
                           c->dstatus, c->st);
             c->launches++;
             TRY(after_launch(c, "adjoint kernel"));
         }
         KTimer t(c, "adj_tc_reduce");
-        launch_adj_tc_reduce(d, c->units, c->cb_off, c->partial, f16 ? c->yscale : nullptr, c->gsum, c->st);
+        launch_adj_tc_reduce(d, c->units, c->cb_off, c->partial, f16 ? c->ymax : nullptr, c->gsum, c->st);
         c->launches++;
         TRY(after_launch(c, "adjoint reduction"));
         *ks_out = 1;
@@ -680,7 +689,7 @@ mem_status run_objgrad(mem_ctx* c, const ImgSrc& src, int projected, float* out3
     void* yout = c->prec == MEM_PREC_FP64_DIRECT ? (void*)c->y64 : (void*)c->y32;
     TRY(run_forward(c, src, FWD_RESID, true, yout));
     int ks = 1;
-    TRY(run_adjoint(c, &ks));
+    TRY(run_adjoint(c, &ks, true));
     {
         KTimer t(c, "finalize");
         launch_finalize(c->dd(), src, c->gsum, ks, projected, out32, full64, proj64, c->st);

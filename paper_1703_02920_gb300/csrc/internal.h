@@ -97,8 +97,10 @@ void launch_colmean(const DevData& d, const ImgSrc& src, float* cmean, float* cm
                     float* pmax, cudaStream_t st);
 int colmean_tmp_count(int N, int C);
 __host__ __device__ inline int colmean_blocks(int N) { return (N + 31) / 32; }
-// yscale[0] = power-of-two scale for max|y| over 2*Z floats (part: 256 floats).
-void launch_absmax_scale(int64_t n, const float* y, float* part, float* yscale, cudaStream_t st);
+// max |component| of n floats into ymax[0]; the FP16X3 adjoint scales y by
+// pow2_scale_for(ymax[0]).  The forward writes the same maximum of the y it
+// produces (RESID mode) when given ymax (zeroed before).
+void launch_absmax(int64_t n, const float* y, float* part, float* ymax, cudaStream_t st);
 int prep_blocks(int N);
 
 void launch_fwd_direct(const DevData& d, int fp64, const VisTile* tiles, int n_tiles, const void* B,
@@ -128,16 +130,19 @@ void launch_grid_interp(const DevData& d, int M, const void* F, int64_t z_total,
 int fwd_rs_max_stages(int N);
 void launch_fwd_rs(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
                    const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,
-                   double2* vpart, int64_t z_total, int num_sms, uint64_t spin, int* status, cudaStream_t st);
+                   float* ymax, double2* vpart, int64_t z_total, int num_sms, uint64_t spin, int* status,
+                   cudaStream_t st);
 // f16 = 1: FP16X3 operands (planes scaled by cscale[c]); 0: BF16X3.
+// ymax (nullable, RESID mode): max |component| of the weighted residual
+// written to yout is combined into ymax[0] (which the caller zeroes).
 void launch_fwd_tc(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
                    const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,
-                   int grid, uint64_t spin, int* status, cudaStream_t st);
+                   float* ymax, int grid, uint64_t spin, int* status, cudaStream_t st);
 int adj_tc_smem_bytes(int N, int stages);
 // units sorted by CTA: CTA b runs units [cta_unit_off[b], cta_unit_off[b+1]).
-// f16 = 1: FP16X3 with y scaled by yscale[0] (partials carry the scale).
+// f16 = 1: FP16X3 with y scaled by pow2_scale_for(ymax[0]) (partials carry the scale).
 void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                   const float2* y, const float* yscale, float* partial, uint64_t spin, int* status,
+                   const float2* y, const float* ymax, float* partial, uint64_t spin, int* status,
                    cudaStream_t st);
 // Variant reading u, v (FP64, wavelengths) instead of the prepared phase
 // increments: the caller passes d.u, d.v, d.dx, d.dy; d.pa / d.pb are unused.
@@ -147,9 +152,9 @@ void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_uni
 void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partial, const float* beam,
                               float* out, cudaStream_t st);
 // Sum unit partials per channel (unit order) into gsum[C][N*N].
-// yscale (nullable): partials are divided by yscale[0].
+// ymax (nullable, FP16X3): partials are divided by pow2_scale_for(ymax[0]).
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* unit_off_by_chan_blk,
-                          const float* partial, const float* yscale, double* gsum, cudaStream_t st);
+                          const float* partial, const float* ymax, double* gsum, cudaStream_t st);
 
 // grad_i = sum_{c in image i} A_c * sum_k gsum[k][c] + lambda (1 + log(I/G)); optional projection.
 void launch_finalize(const DevData& d, const ImgSrc& src, const double* gsum, int ks, int projected,

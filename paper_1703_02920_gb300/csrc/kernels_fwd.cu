@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
     k_fwd_tc(DevData d, const VisTile* __restrict__ tiles, int n_tiles,
              const uint16_t* __restrict__ planes, const float* __restrict__ cmean,
              const float* __restrict__ cscale, int mode, float2* __restrict__ yout,
-             double* __restrict__ chi_part, uint64_t spin, int* status) {
+             double* __restrict__ chi_part, unsigned* __restrict__ ymax_bits, uint64_t spin, int* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ F2Shared S;
     const int N = d.N, c0 = N / 2;
@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             const double q0 = __shfl_xor_sync(0xffffffffu, p0, 16);
             const double q1 = __shfl_xor_sync(0xffffffffu, p1, 16);
             double chi = 0.0;
+            float ym = 0.f;  // max |component| of the weighted residual (RESID mode)
             if (valid && comp == 0) {
                 const double Vre = p0 - q1;  // ReEx ReT - ImEx ImT
                 const double Vim = q0 + p1;  // ReEx ImT + ImEx ReT
@@ -342,8 +343,18 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                     }
                     const double w = d.w[j];
                     chi = 0.5 * w * (rr * rr + ri * ri);
-                    if (mode == FWD_RESID) yout[j] = make_float2((float)(w * rr), (float)(w * ri));
+                    if (mode == FWD_RESID) {
+                        const float2 yv = make_float2((float)(w * rr), (float)(w * ri));
+                        yout[j] = yv;
+                        ym = fmaxf(fabsf(yv.x), fabsf(yv.y));
+                    }
                 }
+            }
+            if (mode == FWD_RESID && ymax_bits) {
+                // order-independent maximum (non-negative floats order as their bits)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) ym = fmaxf(ym, __shfl_down_sync(0xffffffffu, ym, o));
+                if (lane == 0) atomicMax(ymax_bits, __float_as_uint(ym));
             }
             if (mode != FWD_VIS) {
                 // one partial per warp (16 visibilities), summed later in a fixed order
@@ -369,25 +380,27 @@ int fwd_tc_smem_bytes(int BN, int stages) { return stages * f2_stage_bytes(BN) +
 template <bool F16, int STAGES>
 static void launch_fwd_variant(const DevData& d, const VisTile* tiles, int n_tiles, const void* planes,
                                const float* cmean, const float* cscale, int mode, float2* yout,
-                               double* chi_part, int grid, uint64_t spin, int* status, cudaStream_t st) {
+                               double* chi_part, unsigned* ymax_bits, int grid, uint64_t spin, int* status,
+                               cudaStream_t st) {
     const int smem = fwd_tc_smem_bytes(d.fwd_bn, STAGES);
     cudaFuncSetAttribute(k_fwd_tc<F16, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_fwd_tc<F16, STAGES><<<grid, F2_THREADS, smem, st>>>(d, tiles, n_tiles, (const uint16_t*)planes, cmean,
-                                                          cscale, mode, yout, chi_part, spin, status);
+                                                          cscale, mode, yout, chi_part, ymax_bits, spin, status);
 }
 
 void launch_fwd_tc(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
                    const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,
-                   int grid, uint64_t spin, int* status, cudaStream_t st) {
+                   float* ymax, int grid, uint64_t spin, int* status, cudaStream_t st) {
+    unsigned* ymax_bits = (unsigned*)ymax;
     if (n_tiles <= 0) return;
     if (grid > n_tiles) grid = n_tiles;
     const bool s3 = d.fwd_stages == 3;
     if (f16) {
-        if (s3) launch_fwd_variant<true, 3>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, grid, spin, status, st);
-        else launch_fwd_variant<true, 4>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, grid, spin, status, st);
+        if (s3) launch_fwd_variant<true, 3>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, ymax_bits, grid, spin, status, st);
+        else launch_fwd_variant<true, 4>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, ymax_bits, grid, spin, status, st);
     } else {
-        if (s3) launch_fwd_variant<false, 3>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, grid, spin, status, st);
-        else launch_fwd_variant<false, 4>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, grid, spin, status, st);
+        if (s3) launch_fwd_variant<false, 3>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, ymax_bits, grid, spin, status, st);
+        else launch_fwd_variant<false, 4>(d, tiles, n_tiles, planes, cmean, cscale, mode, yout, chi_part, ymax_bits, grid, spin, status, st);
     }
 }
 

@@ -339,11 +339,13 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
 // visibilities, the layout the scalar reduction reads (4 per tile).
 __global__ void __launch_bounds__(64) k_fwd_combine(DevData d, const VisTile* __restrict__ tiles,
                                                     const double2* __restrict__ vpart, int n_slices,
-                                                    int64_t z_total, int mode, float2* yout, double* chi_part) {
+                                                    int64_t z_total, int mode, float2* yout, double* chi_part,
+                                                    unsigned* ymax_bits) {
     const int t = blockIdx.x;
     const VisTile tl = tiles[t];
     const int jv = threadIdx.x;
     double chi = 0.0;
+    float ym = 0.f;  // max |component| of the weighted residual (RESID mode)
     if (jv < tl.count) {
         const int64_t j = tl.start + jv;
         double Vre = 0.0, Vim = 0.0;
@@ -365,8 +367,18 @@ __global__ void __launch_bounds__(64) k_fwd_combine(DevData d, const VisTile* __
             }
             const double w = d.w[j];
             chi = 0.5 * w * (rr * rr + ri * ri);
-            if (mode == FWD_RESID) yout[j] = make_float2((float)(w * rr), (float)(w * ri));
+            if (mode == FWD_RESID) {
+                const float2 yv = make_float2((float)(w * rr), (float)(w * ri));
+                yout[j] = yv;
+                ym = fmaxf(fabsf(yv.x), fabsf(yv.y));
+            }
         }
+    }
+    if (mode == FWD_RESID && ymax_bits) {
+        // order-independent maximum (non-negative floats order as their bits)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ym = fmaxf(ym, __shfl_down_sync(0xffffffffu, ym, o));
+        if ((jv & 31) == 0) atomicMax(ymax_bits, __float_as_uint(ym));
     }
     if (mode != FWD_VIS) {
 #pragma unroll
@@ -397,7 +409,8 @@ int fwd_rs_max_stages(int N) {
 
 void launch_fwd_rs(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
                    const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,
-                   double2* vpart, int64_t z_total, int num_sms, uint64_t spin, int* status, cudaStream_t st) {
+                   float* ymax, double2* vpart, int64_t z_total, int num_sms, uint64_t spin, int* status,
+                   cudaStream_t st) {
     if (n_tiles <= 0) return;
     const int n_slices = d.N / fwd_rs_ks(d.N);
     // CTAs per slice: one per SM, at most one per tile
@@ -415,7 +428,8 @@ void launch_fwd_rs(const DevData& d, int f16, const VisTile* tiles, int n_tiles,
         else MSK_RS(false, 6);
     }
 #undef MSK_RS
-    k_fwd_combine<<<n_tiles, 64, 0, st>>>(d, tiles, vpart, n_slices, z_total, mode, yout, chi_part);
+    k_fwd_combine<<<n_tiles, 64, 0, st>>>(d, tiles, vpart, n_slices, z_total, mode, yout, chi_part,
+                                          (unsigned*)ymax);
 }
 
 }  // namespace msk

@@ -192,16 +192,16 @@ __global__ void __launch_bounds__(256) k_absmax_part(int64_t n, const float* __r
     }
 }
 
-__global__ void k_absmax_final(const float* __restrict__ part, float* yscale) {
+__global__ void k_absmax_final(const float* __restrict__ part, float* ymax) {
     if (threadIdx.x != 0) return;
     float t = 0.f;
     for (int k = 0; k < 256; ++k) t = fmaxf(t, part[k]);
-    yscale[0] = pow2_scale_for(t);
+    ymax[0] = t;
 }
 
-void launch_absmax_scale(int64_t n, const float* y, float* part, float* yscale, cudaStream_t st) {
+void launch_absmax(int64_t n, const float* y, float* part, float* ymax, cudaStream_t st) {
     k_absmax_part<<<256, 256, 0, st>>>(n, y, part);
-    k_absmax_final<<<1, 32, 0, st>>>(part, yscale);
+    k_absmax_final<<<1, 32, 0, st>>>(part, ymax);
 }
 
 __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, void* bout,
@@ -482,16 +482,18 @@ void launch_finalize(const DevData& d, const ImgSrc& src, const double* gsum, in
 // Ordered FP64 reductions of tile partials into per-image and total scalars.
 // scal layout: [0..2] = Phi, chi^2, S totals; [3 + 3i ...] per image.
 // ---------------------------------------------------------------------------
-// Stage 1: grid (images, SCAL_SPLIT); block (i, q) sums a contiguous share of
-// image i's chi^2 partials and entropy partials in a fixed order.
+// Grid (images, SCAL_SPLIT); block (i, q) sums a contiguous share of image
+// i's chi^2 partials and entropy partials in a fixed order; the last block to
+// finish adds the shares in order.
 constexpr int SCAL_SPLIT = 32;
 
-__global__ void __launch_bounds__(256) k_scalars_part(DevData d, const int* __restrict__ tile_off,
-                                                      const double* __restrict__ chi_part,
-                                                      const double* __restrict__ ent_part,
-                                                      int with_entropy, int n_ent_blocks,
-                                                      double* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_scalars(DevData d, const int* __restrict__ tile_off,
+                                                 const double* __restrict__ chi_part,
+                                                 const double* __restrict__ ent_part, int with_entropy,
+                                                 int n_ent_blocks, double* part, double* img_tmp, double* scal,
+                                                 unsigned* counter) {
     __shared__ double sh[8];
+    __shared__ bool last;
     const int i = blockIdx.x, q = blockIdx.y;
     int c_lo = d.shared ? 0 : i, c_hi = d.shared ? d.C : i + 1;
     const int64_t t0 = 4LL * tile_off[c_lo], t1 = 4LL * tile_off[c_hi];  // channels are contiguous
@@ -510,51 +512,55 @@ __global__ void __launch_bounds__(256) k_scalars_part(DevData d, const int* __re
     if (threadIdx.x == 0) {
         part[((int64_t)i * SCAL_SPLIT + q) * 2] = chi;
         part[((int64_t)i * SCAL_SPLIT + q) * 2 + 1] = S;
+        // the last block to finish forms the totals
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
     }
-}
-
-// Stage 2: one thread per image sums its SCAL_SPLIT partials in order; thread
-// 0 then forms the totals in image order.
-__global__ void k_scalars_total(int n_images, double lambda, const double* __restrict__ part,
-                                double* img_tmp, double* scal) {
-    for (int i = threadIdx.x; i < n_images; i += blockDim.x) {
-        double chi = 0.0, S = 0.0;
-        for (int q = 0; q < SCAL_SPLIT; ++q) {
-            chi += part[((int64_t)i * SCAL_SPLIT + q) * 2];
-            S += part[((int64_t)i * SCAL_SPLIT + q) * 2 + 1];
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // Stage 2 (last block): one thread per image sums its SCAL_SPLIT partials
+    // in order (read through L2); thread 0 then forms the totals in image order
+    for (int im = threadIdx.x; im < d.n_images; im += blockDim.x) {
+        double c2 = 0.0, s2 = 0.0;
+        for (int k = 0; k < SCAL_SPLIT; ++k) {
+            c2 += __ldcg(part + ((int64_t)im * SCAL_SPLIT + k) * 2);
+            s2 += __ldcg(part + ((int64_t)im * SCAL_SPLIT + k) * 2 + 1);
         }
-        img_tmp[3 * i] = chi - lambda * S;
-        img_tmp[3 * i + 1] = chi;
-        img_tmp[3 * i + 2] = S;
-        scal[3 + 3 * i] = chi - lambda * S;
-        scal[4 + 3 * i] = chi;
-        scal[5 + 3 * i] = S;
+        img_tmp[3 * im] = c2 - d.lambda * s2;
+        img_tmp[3 * im + 1] = c2;
+        img_tmp[3 * im + 2] = s2;
+        scal[3 + 3 * im] = c2 - d.lambda * s2;
+        scal[4 + 3 * im] = c2;
+        scal[5 + 3 * im] = s2;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0, b = 0, c = 0;
-        for (int i = 0; i < n_images; ++i) {
-            a += img_tmp[3 * i];
-            b += img_tmp[3 * i + 1];
-            c += img_tmp[3 * i + 2];
+        double ta = 0, tb = 0, tc = 0;
+        for (int im = 0; im < d.n_images; ++im) {
+            ta += img_tmp[3 * im];
+            tb += img_tmp[3 * im + 1];
+            tc += img_tmp[3 * im + 2];
         }
-        scal[0] = a;
-        scal[1] = b;
-        scal[2] = c;
+        scal[0] = ta;
+        scal[1] = tb;
+        scal[2] = tc;
+        *counter = 0;  // ready for the next evaluation
     }
 }
 
 void launch_scalars(const DevData& d, const int* tile_off, const double* chi_part,
                     const double* ent_part, int with_entropy, double* scal, double* img_tmp,
                     cudaStream_t st) {
-    // img_tmp holds 3 * n_images + 2 * SCAL_SPLIT * n_images doubles
+    // img_tmp: 3 * n_images totals, 2 * SCAL_SPLIT * n_images partials, then the
+    // completion counter (zero between evaluations)
     double* part = img_tmp + 3 * d.n_images;
-    k_scalars_part<<<dim3(d.n_images, SCAL_SPLIT), 256, 0, st>>>(d, tile_off, chi_part, ent_part,
-                                                                  with_entropy, prep_blocks(d.N), part);
-    k_scalars_total<<<1, 256, 0, st>>>(d.n_images, d.lambda, part, img_tmp, scal);
+    unsigned* counter = (unsigned*)(part + 2 * SCAL_SPLIT * d.n_images);
+    k_scalars<<<dim3(d.n_images, SCAL_SPLIT), 256, 0, st>>>(d, tile_off, chi_part, ent_part, with_entropy,
+                                                             prep_blocks(d.N), part, img_tmp, scal, counter);
 }
 
-int scalars_tmp_doubles(int n_images) { return 3 * n_images + 2 * 32 * n_images; }
+int scalars_tmp_doubles(int n_images) { return 3 * n_images + 2 * SCAL_SPLIT * n_images + 1; }
 
 // ---------------------------------------------------------------------------
 // a8: CG vector kernels (FP64), per image.

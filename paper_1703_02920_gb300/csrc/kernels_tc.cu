@@ -124,13 +124,13 @@ struct AdjShared {
 
 // FROM_UV: phase increments reduced from u, v inside the producers instead of
 // read from the prepared arrays.
-// F16: FP16X3 operands with y scaled by yscale[0] (a power of two, undone
-// when the partials are summed); otherwise BF16X3.
+// F16: FP16X3 operands with y scaled by pow2_scale_for(ymax[0]) (a power of
+// two, undone when the partials are summed); otherwise BF16X3.
 // ADJ_STAGES: depth of the shared-memory pipeline (autotuned).
 template <bool FROM_UV, bool F16, int ADJ_STAGES>
 __global__ void __launch_bounds__(ADJ_THREADS, 1)
     k_adj_tc(DevData d, const AdjUnit* __restrict__ units, const int* __restrict__ cta_unit_off,
-             const float2* __restrict__ y, const float* __restrict__ yscale, float* __restrict__ partial,
+             const float2* __restrict__ y, const float* __restrict__ ymax, float* __restrict__ partial,
              uint64_t spin, int* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ AdjShared S;
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
         const int side_grp = ey_side ? (ptid >> 4) : (ptid >> 4) - n_groups / 2;
         const int jj = ptid & 15;           // visibility within the stage
         const int ngA = R / 8, ngB = BLK / 8;
-        const float ysc = F16 ? yscale[0] : 1.f;
+        const float ysc = F16 ? pow2_scale_for(ymax[0]) : 1.f;
         uint32_t sc = 0, dr = 0;  // stages produced; accumulator drains (warps 0-3)
         bool ok = true;
         for (int u = u0; u < u1 && ok; ++u) {
@@ -360,25 +360,25 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
 
 template <bool FROM_UV, bool F16, int STAGES>
 static void launch_adj_variant(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                               const float2* y, const float* yscale, float* partial, uint64_t spin,
+                               const float2* y, const float* ymax, float* partial, uint64_t spin,
                                int* status, cudaStream_t st) {
     const int smem = adj_tc_smem_bytes(d.N, STAGES);
     cudaFuncSetAttribute(k_adj_tc<FROM_UV, F16, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_adj_tc<FROM_UV, F16, STAGES><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, yscale,
+    k_adj_tc<FROM_UV, F16, STAGES><<<n_ctas, ADJ_THREADS, smem, st>>>(d, units, cta_unit_off, y, ymax,
                                                                       partial, spin, status);
 }
 
 void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
-                   const float2* y, const float* yscale, float* partial, uint64_t spin, int* status,
+                   const float2* y, const float* ymax, float* partial, uint64_t spin, int* status,
                    cudaStream_t st) {
     if (n_ctas <= 0) return;
     const bool s2 = d.adj_stages == 2;
     if (f16) {
-        if (s2) launch_adj_variant<false, true, 2>(d, units, cta_unit_off, n_ctas, y, yscale, partial, spin, status, st);
-        else launch_adj_variant<false, true, 3>(d, units, cta_unit_off, n_ctas, y, yscale, partial, spin, status, st);
+        if (s2) launch_adj_variant<false, true, 2>(d, units, cta_unit_off, n_ctas, y, ymax, partial, spin, status, st);
+        else launch_adj_variant<false, true, 3>(d, units, cta_unit_off, n_ctas, y, ymax, partial, spin, status, st);
     } else {
-        if (s2) launch_adj_variant<false, false, 2>(d, units, cta_unit_off, n_ctas, y, yscale, partial, spin, status, st);
-        else launch_adj_variant<false, false, 3>(d, units, cta_unit_off, n_ctas, y, yscale, partial, spin, status, st);
+        if (s2) launch_adj_variant<false, false, 2>(d, units, cta_unit_off, n_ctas, y, ymax, partial, spin, status, st);
+        else launch_adj_variant<false, false, 3>(d, units, cta_unit_off, n_ctas, y, ymax, partial, spin, status, st);
     }
 }
 
@@ -420,7 +420,7 @@ void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partia
 // gsum[c][N*N] (without the beam factor).
 __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __restrict__ cb_unit_off,
                                                        const float* __restrict__ partial,
-                                                       const float* __restrict__ yscale,
+                                                       const float* __restrict__ ymax,
                                                        double* __restrict__ gsum) {
     const int N = d.N;
     const int64_t NN = (int64_t)N * N;
@@ -451,15 +451,15 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __r
         for (int k = 0; k < 8; ++k) two_sum_acc(s, comp, q[k]);
     }
     for (; u < u1; ++u) two_sum_acc(s, comp, __ldg(src + (int64_t)u * stride));
-    const double inv = yscale ? 1.0 / (double)yscale[0] : 1.0;
+    const double inv = ymax ? 1.0 / (double)pow2_scale_for(ymax[0]) : 1.0;
     gsum[(int64_t)c * NN + p] = ((double)s + (double)comp) * inv;
 }
 
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* cb_unit_off,
-                          const float* partial, const float* yscale, double* gsum, cudaStream_t st) {
+                          const float* partial, const float* ymax, double* gsum, cudaStream_t st) {
     (void)units;
     dim3 grid(prep_blocks(d.N), d.C);
-    k_adj_tc_reduce<<<grid, 256, 0, st>>>(d, cb_unit_off, partial, yscale, gsum);
+    k_adj_tc_reduce<<<grid, 256, 0, st>>>(d, cb_unit_off, partial, ymax, gsum);
 }
 
 }  // namespace msk
