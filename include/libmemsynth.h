@@ -124,7 +124,7 @@ const char *mem_status_string(mem_status s);
 /* Switch the number format used by later calls (same data, no re-upload). */
 mem_status mem_set_precision(mem_ctx *ctx, int32_t precision);
 
-/* Sizes: total visibilities, channels, images (C or 1), image side. */
+/* Sizes: total visibilities; images (C in cube mode, 1 in shared mode). */
 int64_t mem_num_vis(const mem_ctx *ctx);
 int32_t mem_num_images(const mem_ctx *ctx);
 
@@ -156,8 +156,14 @@ mem_status mem_objective_grad_host(mem_ctx *ctx, const float *image_host, float 
 const double *mem_scalars_dev(const mem_ctx *ctx);
 
 /* Minimise Phi over I >= G (Eq. minproblem) from image_dev_inout (clipped to
- * G first), n_iter projected Polak-Ribiere CG iterations per image, each with
- * a bracketing + Brent line search.  Cube mode runs one independent CG per
+ * G first), n_iter projected Polak-Ribiere CG iterations per image (beta
+ * clipped at 0, steepest-descent restart every 50 iterations or when the
+ * direction is not a descent one), each with a line search on
+ * phi(alpha) = Phi(max(I + alpha d, G)): first trial step from the quadratic
+ * model of chi^2 along d, bracketing, Brent's method (relative tolerance 1e-3,
+ * at most 20 evaluations), then one Newton step on central differences.  Each
+ * probe evaluates the change of Phi from the image difference, so its
+ * rounding scales with the step.  Cube mode runs one independent CG per
  * channel image, all channels batched in every launch.  hist_host (nullable,
  * host) receives per image and iteration 0..n_iter the 6 doubles (Phi, chi^2,
  * S, alpha, beta, evaluations), laid out [image][iteration][6]; iterations
