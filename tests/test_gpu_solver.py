@@ -62,6 +62,12 @@ def test_solve_matches_oracle(ms, solve_ref, oracle_mod, form):
     rel = np.linalg.norm(img - ref_img) / np.linalg.norm(ref_img)
     ref_phi = ref_hist[-1]["phi"]
     assert rel <= 1e-3, rel
+    # the bound-constrained first-order residual (KKT) fell over the solve
+    P = oracle_mod.Problem.from_dataset(ds)
+    I_start = np.full((1, ds.N, ds.N), float(np.float32(ds.G)))
+    k0 = oracle_mod.kkt_residual(I_start, oracle_mod.objective_grad(P, I_start)[3], P.G)
+    k1 = oracle_mod.kkt_residual(img.reshape(1, ds.N, ds.N), oracle_mod.objective_grad(P, img.reshape(1, ds.N, ds.N))[3], P.G)
+    assert k1 < 0.1 * k0, (k0, k1)
     if form == "fp64_direct":
         assert abs(rep.phi - ref_phi) <= 1e-6 * abs(ref_phi), (rep.phi, ref_phi)
     else:
