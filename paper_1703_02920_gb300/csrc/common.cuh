@@ -260,4 +260,75 @@ __device__ __forceinline__ void split16x2(float a, float b, uint32_t& hi, uint32
     else split_bf16x2(a, b, hi, lo);
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32x2 forms (sm_100 and later) of the table arithmetic above.
+// Results are bit-identical to cmul / split16x2: every component sees the
+// same roundings in the same order, two lanes per instruction.
+// ---------------------------------------------------------------------------
+
+// Eight rotation factors w_0..w_7 in planar pairs: x[p] = (Re w_2p, Re w_2p+1),
+// y[p] the imaginary parts.
+struct Rot8 {
+    float2 x[4], y[4];
+};
+
+__device__ __forceinline__ Rot8 rot8_of(const cf2 (&w)[8]) {
+    Rot8 r;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        r.x[p] = make_float2(w[2 * p].x, w[2 * p + 1].x);
+        r.y[p] = make_float2(w[2 * p].y, w[2 * p + 1].y);
+    }
+    return r;
+}
+
+// z_q = base w_q for q = 0..7 as planar pairs re[p] = (Re z_2p, Re z_2p+1),
+// im[p] likewise: Re z = fma(bx, wx, (-by) wy), Im z = fma(bx, wy, by wx),
+// exactly as cmul(base, w_q).
+__device__ __forceinline__ void rotate8(cf2 base, const Rot8& w, float2 (&re)[4], float2 (&im)[4]) {
+    const float2 bx = make_float2(base.x, base.x), by = make_float2(base.y, base.y);
+    const float2 nby = make_float2(-base.y, -base.y);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        re[p] = __ffma2_rn(bx, w.x[p], __fmul2_rn(nby, w.y[p]));
+        im[p] = __ffma2_rn(bx, w.y[p], __fmul2_rn(by, w.x[p]));
+    }
+}
+
+// split16x2 of the pair v = (a, b): the residual a - hi, b - hi in one
+// packed subtraction.
+template <bool F16>
+__device__ __forceinline__ void split16x2p(float2 v, uint32_t& hi, uint32_t& lo) {
+    if (F16) {
+        const __half2 h = __float22half2_rn(v);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __float22half2_rn(__fadd2_rn(v, make_float2(-hf.x, -hf.y)));
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    } else {
+        const __nv_bfloat162 h = __float22bfloat162_rn(v);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __float22bfloat162_rn(__fadd2_rn(v, make_float2(-hf.x, -hf.y)));
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    }
+}
+
+// Eight rotated entries split into the four 16-byte operand rows of one
+// 8-element group: Re hi/lo and Im hi/lo.
+template <bool F16>
+__device__ __forceinline__ void table8_split(cf2 base, const Rot8& w, uint4& rh, uint4& rl, uint4& ih,
+                                             uint4& il) {
+    float2 re[4], im[4];
+    rotate8(base, w, re, im);
+    split16x2p<F16>(re[0], rh.x, rl.x);
+    split16x2p<F16>(re[1], rh.y, rl.y);
+    split16x2p<F16>(re[2], rh.z, rl.z);
+    split16x2p<F16>(re[3], rh.w, rl.w);
+    split16x2p<F16>(im[0], ih.x, il.x);
+    split16x2p<F16>(im[1], ih.y, il.y);
+    split16x2p<F16>(im[2], ih.z, il.z);
+    split16x2p<F16>(im[3], ih.w, il.w);
+}
+
 }  // namespace msk

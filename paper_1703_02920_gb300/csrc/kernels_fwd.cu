@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             cf2 step[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) step[q] = cis_neg(phase_mul(q, pb));
+            const Rot8 w = rot8_of(step);
             for (int mb = 0; mb < n_mb && ok; ++mb) {
                 for (int ks = 0; ks < nk; ++ks, ++sc) {
                     const int s = sc % F2_STAGES;
@@ -203,18 +204,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                     uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
                     if (valid) {
                         const int n0 = ks * TC_BK + g * 8;
-                        const cf2 base = cis_neg(phase_mul(n0 - c0, pb));
-                        cf2 z[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) z[q] = cmul(base, step[q]);
-                        split16x2<F16>(z[0].x, z[1].x, rh.x, rl.x);
-                        split16x2<F16>(z[2].x, z[3].x, rh.y, rl.y);
-                        split16x2<F16>(z[4].x, z[5].x, rh.z, rl.z);
-                        split16x2<F16>(z[6].x, z[7].x, rh.w, rl.w);
-                        split16x2<F16>(z[0].y, z[1].y, ih.x, il.x);
-                        split16x2<F16>(z[2].y, z[3].y, ih.y, il.y);
-                        split16x2<F16>(z[4].y, z[5].y, ih.z, il.z);
-                        split16x2<F16>(z[6].y, z[7].y, ih.w, il.w);
+                        table8_split<F16>(cis_neg(phase_mul(n0 - c0, pb)), w, rh, rl, ih, il);
                     }
                     ok = __all_sync(0xffffffffu, mbar_wait(&S.empty[s], ((sc / F2_STAGES) & 1) ^ 1, spin,
                                                            abort, status, 64));
