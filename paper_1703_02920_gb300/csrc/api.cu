@@ -810,7 +810,7 @@ bool tune_valid(const mem_ctx* c, const mem_tiling_t& t) {
     const int bn = t.fwd_cols;
     if (bn < 32 || bn > 256 || c->N % bn != 0 || bn % 32 != 0) return false;
     if (!(t.fwd_stages == 3 || t.fwd_stages == 4)) return false;
-    return fwd_tc_smem_bytes(bn, t.fwd_stages) <= 227 * 1024;
+    return fwd_tc_smem_bytes(c->N, bn, t.fwd_stages) <= 227 * 1024;
 }
 
 mem_tiling_t tiling_of(const mem_ctx* c) {
@@ -844,6 +844,8 @@ void default_tiling(mem_ctx* c) {
         t.fwd_stages = 4;
     }
     t.adj_stages = 3;
+    // very large N: the epilogue's column-mean copies leave room for 3 stages
+    if (t.fwd_kernel == MEM_FWD_STREAM && fwd_tc_smem_bytes(c->N, t.fwd_cols, 4) > 227 * 1024) t.fwd_stages = 3;
     apply_tiling(c, t);
 }
 

@@ -111,7 +111,7 @@ void launch_adj_direct(const DevData& d, int fp64, const void* y, double* gsum, 
 int adj_direct_splits(const DevData& d, int num_sms);
 
 // Tensor-core forms.
-int fwd_tc_smem_bytes(int BN, int stages);
+int fwd_tc_smem_bytes(int N, int BN, int stages);
 // Resident-operand forward (N <= 256): the image rows are cut into slices of
 // fwd_rs_ks(N); each CTA keeps one slice of the operand planes in shared
 // memory; slice partials (FP64, [slice][visibility]) are combined by a second

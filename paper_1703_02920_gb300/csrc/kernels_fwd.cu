@@ -230,20 +230,45 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
         const int jv = 16 * warp + (lane & 15), comp = lane >> 4;
         uint32_t it = 0;
         bool ok = true;
+        // this warp's copy of the tile channel's column means (read as
+        // broadcasts; refreshed when the channel changes)
+        float* cmw = (float*)(smem + F2_STAGES * stage_bytes) + warp * N;
+        int cm_chan = -1;
+        // per-visibility inputs are loaded one tile ahead: the next tile's
+        // descriptor and phases arrive while this tile's accumulator drains
+        VisTile tl_next{};
+        uint64_t pa_next = 0, pb_next = 0;
+        auto load_phases = [&](const VisTile& tn) {
+            const int64_t jn = tn.start + (jv < tn.count ? jv : 0);
+            pa_next = d.pa[jn];
+            pb_next = d.pb[jn];
+        };
+        if ((int)blockIdx.x < n_tiles) {
+            tl_next = tiles[blockIdx.x];
+            load_phases(tl_next);
+        }
         for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-            const VisTile tl = tiles[t];
+            const VisTile tl = tl_next;
             const bool valid = jv < tl.count;
             const int64_t j = tl.start + (valid ? jv : 0);
-            const uint64_t pa = d.pa[j];
+            const uint64_t pa = pa_next, pb = pb_next;
+            if (t + (int)gridDim.x < n_tiles) tl_next = tiles[t + gridDim.x];
+            if (tl.chan != cm_chan) {
+                __syncwarp();
+                const float4* src = (const float4*)(cmean + (int64_t)tl.chan * N);
+                for (int i = lane; i < N / 4; i += 32) ((float4*)cmw)[i] = __ldg(src + i);
+                __syncwarp();
+                cm_chan = tl.chan;
+            }
             cf2 step[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) step[q] = cis_neg(phase_mul(q, pa));
+            const Rot8 wx8 = rot8_of(step);
             const cf2 step8 = cis_neg(phase_mul(8, pa));
             // this lane's component of S_j = sum_n Ey[j,n] (accurate sincospi of
             // the exact half-turn and N/2-multiple phases)
             float scomp;
             {
-                const uint64_t pb = d.pb[j];
                 const float th = (float)(int64_t)((int64_t)pb >> 1) * 5.421010862427522e-20f;  // b/2, turns
                 const float tn = (float)(int64_t)phase_mul(N / 2, pb) * 5.421010862427522e-20f;  // N b/2
                 float sh, ch;
@@ -254,7 +279,6 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             }
             const float osc = F16 ? cscale[tl.chan] : 1.f;  // operand scale (power of two)
             scomp *= osc;
-            const float* cm = cmean + (int64_t)tl.chan * N;
             float s0 = 0.f, s1 = 0.f, c0s = 0.f, c1s = 0.f;  // compensated sums
             for (int mb = 0; mb < n_mb; ++mb, ++it) {
                 const int b = it & 1;
@@ -263,35 +287,37 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * BN);
-                // software pipeline over 16-column chunks: the TMEM load and the
-                // column means of chunk q+1 are in flight while chunk q is reduced
+                // software pipeline over 16-column chunks: the TMEM load of
+                // chunk q+1 is in flight while chunk q is reduced
                 const int nq = BN / 16;
                 uint32_t tv[2][16];
-                float4 cq4[2][4];
-                auto load_chunk = [&](int q, int slot) {
-                    tmem_ld16(lane_base + q * 16, tv[slot]);
-                    const float4* src = (const float4*)(cm + mb * BN + q * 16);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) cq4[slot][k] = __ldg(src + k);
-                };
+                auto load_chunk = [&](int q, int slot) { tmem_ld16(lane_base + q * 16, tv[slot]); };
                 // sum_k Ex[m0+k] t_k = base * sum_{k<8} step_k t_k + base8 * sum_{k<8} step_k t_{k+8}
                 auto reduce_chunk = [&](int q, int slot) {
                     const int m0 = mb * BN + q * 16;
                     const cf2 base = cis_neg(phase_mul(m0 - c0, pa));
                     const cf2 base8 = cmul(base, step8);
-                    const float* cq = (const float*)cq4[slot];
-                    float ux = 0.f, uy = 0.f, wx = 0.f, wy = 0.f;
+                    float2 cq[8];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const float tk = fmaf(cq[k], scomp, __uint_as_float(tv[slot][k]));
-                        const float tw = fmaf(cq[k + 8], scomp, __uint_as_float(tv[slot][k + 8]));
-                        ux = fmaf(step[k].x, tk, ux);
-                        uy = fmaf(step[k].y, tk, uy);
-                        wx = fmaf(step[k].x, tw, wx);
-                        wy = fmaf(step[k].y, tw, wy);
+                    for (int k = 0; k < 4; ++k) *(float4*)(cq + 2 * k) = ((const float4*)(cmw + m0))[k];
+                    // packed pairs (even k, odd k), added at the end
+                    const float2 ss = make_float2(scomp, scomp);
+                    float2 ux = {0.f, 0.f}, uy = {0.f, 0.f}, wx = {0.f, 0.f}, wy = {0.f, 0.f};
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const float2 tk = __ffma2_rn(cq[p], ss, make_float2(__uint_as_float(tv[slot][2 * p]),
+                                                                            __uint_as_float(tv[slot][2 * p + 1])));
+                        const float2 tw = __ffma2_rn(cq[p + 4], ss,
+                                                     make_float2(__uint_as_float(tv[slot][2 * p + 8]),
+                                                                 __uint_as_float(tv[slot][2 * p + 9])));
+                        ux = __ffma2_rn(wx8.x[p], tk, ux);
+                        uy = __ffma2_rn(wx8.y[p], tk, uy);
+                        wx = __ffma2_rn(wx8.x[p], tw, wx);
+                        wy = __ffma2_rn(wx8.y[p], tw, wy);
                     }
-                    const float a0 = fmaf(base.x, ux, fmaf(-base.y, uy, fmaf(base8.x, wx, -base8.y * wy)));
-                    const float a1 = fmaf(base.x, uy, fmaf(base.y, ux, fmaf(base8.x, wy, base8.y * wx)));
+                    const float sux = ux.x + ux.y, suy = uy.x + uy.y, swx = wx.x + wx.y, swy = wy.x + wy.y;
+                    const float a0 = fmaf(base.x, sux, fmaf(-base.y, suy, fmaf(base8.x, swx, -base8.y * swy)));
+                    const float a1 = fmaf(base.x, suy, fmaf(base.y, sux, fmaf(base8.x, swy, base8.y * swx)));
                     two_sum_acc(s0, c0s, a0);
                     two_sum_acc(s1, c1s, a1);
                 };
@@ -310,6 +336,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                 if (lane == 0) mbar_arrive(&S.tempty[b]);
             }
             if (!ok) break;
+            if (t + (int)gridDim.x < n_tiles) load_phases(tl_next);
             // lane < 16: (sum ReEx ReT, sum ImEx ReT); lane >= 16: (sum ReEx ImT, sum ImEx ImT)
             const double inv = 1.0 / (double)osc;
             const double p0 = ((double)s0 + (double)c0s) * inv, p1 = ((double)s1 + (double)c1s) * inv;
@@ -365,14 +392,15 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
 
 }  // namespace
 
-int fwd_tc_smem_bytes(int BN, int stages) { return stages * f2_stage_bytes(BN) + 1024; }
+// stage ring + the epilogue warps' column-mean copies (4 x N floats) + alignment
+int fwd_tc_smem_bytes(int N, int BN, int stages) { return stages * f2_stage_bytes(BN) + 16 * N + 1024; }
 
 template <bool F16, int STAGES>
 static void launch_fwd_variant(const DevData& d, const VisTile* tiles, int n_tiles, const void* planes,
                                const float* cmean, const float* cscale, int mode, float2* yout,
                                double* chi_part, unsigned* ymax_bits, int grid, uint64_t spin, int* status,
                                cudaStream_t st) {
-    const int smem = fwd_tc_smem_bytes(d.fwd_bn, STAGES);
+    const int smem = fwd_tc_smem_bytes(d.N, d.fwd_bn, STAGES);
     cudaFuncSetAttribute(k_fwd_tc<F16, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_fwd_tc<F16, STAGES><<<grid, F2_THREADS, smem, st>>>(d, tiles, n_tiles, (const uint16_t*)planes, cmean,
                                                           cscale, mode, yout, chi_part, ymax_bits, spin, status);
