@@ -257,6 +257,8 @@ struct mem_ctx {
     double *u = nullptr, *v = nullptr, *w = nullptr;
     uint64_t *pa = nullptr, *pb = nullptr;
     double2* vo = nullptr;
+    float4* vo32 = nullptr;  // V° as FP32 (hi, lo) pairs, for the tensor-core epilogues
+    float* w32 = nullptr;
     float* beam = nullptr;
     int64_t* doff = nullptr;
 
@@ -349,6 +351,8 @@ struct mem_ctx {
         d.v = v;
         d.vo = vo;
         d.w = w;
+        d.vo32 = vo32;
+        d.w32 = w32;
         d.beam = beam;
         d.off = doff;
         d.dx = dx;
@@ -1279,6 +1283,7 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
     if ((s = dalloc(c, &c->u, std::max<int64_t>(Z, 1))) || (s = dalloc(c, &c->v, std::max<int64_t>(Z, 1))) ||
         (s = dalloc(c, &c->w, std::max<int64_t>(Z, 1))) || (s = dalloc(c, &c->pa, std::max<int64_t>(Z, 1))) ||
         (s = dalloc(c, &c->pb, std::max<int64_t>(Z, 1))) || (s = dalloc(c, &c->vo, std::max<int64_t>(Z, 1))) ||
+        (s = dalloc(c, &c->vo32, std::max<int64_t>(Z, 1))) || (s = dalloc(c, &c->w32, std::max<int64_t>(Z, 1))) ||
         (s = dalloc(c, &c->beam, (size_t)C * NN)) || (s = dalloc(c, &c->doff, (size_t)C + 1)) ||
         (s = dalloc(c, &c->dstatus, 1))) {
         g_last_error = c->err;
@@ -1286,6 +1291,14 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
     }
     std::vector<double> wh((size_t)Z);
     for (int64_t k = 0; k < Z; ++k) wh[k] = 1.0 / (sigma[k] * sigma[k]);
+    std::vector<float> w32h((size_t)Z);
+    std::vector<float4> vo32h((size_t)Z);
+    for (int64_t k = 0; k < Z; ++k) {
+        w32h[k] = (float)wh[k];
+        const double re = vis_obs[2 * k], im = vis_obs[2 * k + 1];
+        const float rh = (float)re, ih = (float)im;
+        vo32h[k] = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+    }
     c->wsum_h.assign((size_t)C, 0.0);
     for (int ch = 0; ch < C; ++ch)
         for (int64_t k = c->off[ch]; k < c->off[ch + 1]; ++k) c->wsum_h[ch] += wh[k];
@@ -1296,6 +1309,8 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
     if (e == cudaSuccess) e = cpy(c->v, v, Z * sizeof(double));
     if (e == cudaSuccess) e = cpy(c->w, wh.data(), Z * sizeof(double));
     if (e == cudaSuccess) e = cpy(c->vo, vis_obs, Z * 2 * sizeof(double));
+    if (e == cudaSuccess) e = cpy(c->w32, w32h.data(), Z * sizeof(float));
+    if (e == cudaSuccess) e = cpy(c->vo32, vo32h.data(), Z * sizeof(float4));
     if (e == cudaSuccess) e = cpy(c->beam, pb, C * NN * sizeof(float));
     if (e == cudaSuccess) e = cpy(c->doff, c->off.data(), (C + 1) * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st);

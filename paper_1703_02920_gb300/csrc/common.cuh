@@ -51,6 +51,19 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
     s = t;
 }
 
+// (ah + al) + (bh + bl) for double-float pairs (|al| <= ulp(ah)/2, likewise
+// b), as a normalized pair (hi, lo): Knuth's two-sum of the high parts, then
+// the low parts.  Exact when the high parts cancel (Sterbenz), which is the
+// case for a residual V - V° of a good model.
+__device__ __forceinline__ float2 df_add(float ah, float al, float bh, float bl) {
+    const float s = ah + bh;
+    const float bb = s - ah;
+    const float e = (ah - (s - bb)) + (bh - bb);
+    const float lo = e + (al + bl);
+    const float hi = s + lo;
+    return make_float2(hi, lo - (hi - s));
+}
+
 // exp(-i * angle) components for the forward sign convention are (c, -s).
 struct cf2 { float x, y; };
 

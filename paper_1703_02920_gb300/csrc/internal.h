@@ -40,6 +40,8 @@ struct DevData {
     const double* v;
     const double2* vo;   // observed visibilities
     const double* w;     // 1/sigma^2
+    const float4* vo32;  // observed visibilities as FP32 pairs (Re hi, Im hi, Re lo, Im lo)
+    const float* w32;    // 1/sigma^2 in FP32
     const float* beam;   // C*N*N
     const int64_t* off;  // C+1
     double dx, dy;       // pixel size (radians)

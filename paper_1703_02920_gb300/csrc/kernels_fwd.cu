@@ -337,31 +337,39 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             }
             if (!ok) break;
             if (t + (int)gridDim.x < n_tiles) load_phases(tl_next);
-            // lane < 16: (sum ReEx ReT, sum ImEx ReT); lane >= 16: (sum ReEx ImT, sum ImEx ImT)
-            const double inv = 1.0 / (double)osc;
-            const double p0 = ((double)s0 + (double)c0s) * inv, p1 = ((double)s1 + (double)c1s) * inv;
-            const double q0 = __shfl_xor_sync(0xffffffffu, p0, 16);
-            const double q1 = __shfl_xor_sync(0xffffffffu, p1, 16);
-            double chi = 0.0;
+            // lane < 16: (sum ReEx ReT, sum ImEx ReT); lane >= 16: (sum ReEx ImT, sum ImEx ImT),
+            // each a compensated (hi, lo) pair, unscaled exactly (a power of two).
+            // The tail runs in FP32 pair arithmetic: the residual V - V° is an
+            // exact pair difference, and chi^2 per visibility needs only FP32
+            // relative accuracy (the partials are summed in FP64).
+            const float inv = 1.f / osc;
+            const float p0h = s0 * inv, p0l = c0s * inv, p1h = s1 * inv, p1l = c1s * inv;
+            const float q0h = __shfl_xor_sync(0xffffffffu, p0h, 16), q0l = __shfl_xor_sync(0xffffffffu, p0l, 16);
+            const float q1h = __shfl_xor_sync(0xffffffffu, p1h, 16), q1l = __shfl_xor_sync(0xffffffffu, p1l, 16);
+            float chi = 0.f;
             float ym = 0.f;  // max |component| of the weighted residual (RESID mode)
             if (valid && comp == 0) {
-                const double Vre = p0 - q1;  // ReEx ReT - ImEx ImT
-                const double Vim = q0 + p1;  // ReEx ImT + ImEx ReT
+                const float2 vre = df_add(p0h, p0l, -q1h, -q1l);  // ReEx ReT - ImEx ImT
+                const float2 vim = df_add(q0h, q0l, p1h, p1l);    // ReEx ImT + ImEx ReT
                 if (mode == FWD_VIS) {
-                    yout[j] = make_float2((float)Vre, (float)Vim);
+                    yout[j] = make_float2(vre.x + vre.y, vim.x + vim.y);
                 } else if (mode == FWD_DCHI) {
                     const float2 yv = yout[j];
-                    chi = (double)yv.x * Vre + (double)yv.y * Vim + 0.5 * d.w[j] * (Vre * Vre + Vim * Vim);
+                    const float vr = vre.x + vre.y, vi = vim.x + vim.y;
+                    chi = yv.x * vr + yv.y * vi + 0.5f * d.w32[j] * (vr * vr + vi * vi);
                 } else {
-                    double rr = Vre, ri = Vim;
+                    float rr = vre.x + vre.y, ri = vim.x + vim.y;
                     if (mode != FWD_CURV) {
-                        rr -= d.vo[j].x;
-                        ri -= d.vo[j].y;
+                        const float4 o = d.vo32[j];  // (Re hi, Im hi, Re lo, Im lo)
+                        const float2 r0 = df_add(vre.x, vre.y, -o.x, -o.z);
+                        const float2 r1 = df_add(vim.x, vim.y, -o.y, -o.w);
+                        rr = r0.x + r0.y;
+                        ri = r1.x + r1.y;
                     }
-                    const double w = d.w[j];
-                    chi = 0.5 * w * (rr * rr + ri * ri);
+                    const float w = d.w32[j];
+                    chi = 0.5f * w * (rr * rr + ri * ri);
                     if (mode == FWD_RESID) {
-                        const float2 yv = make_float2((float)(w * rr), (float)(w * ri));
+                        const float2 yv = make_float2(w * rr, w * ri);
                         yout[j] = yv;
                         ym = fmaxf(fabsf(yv.x), fabsf(yv.y));
                     }
@@ -377,7 +385,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                 // one partial per warp (16 visibilities), summed later in a fixed order
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) chi += __shfl_down_sync(0xffffffffu, chi, o);
-                if (lane == 0) chi_part[(int64_t)t * 4 + warp] = chi;
+                if (lane == 0) chi_part[(int64_t)t * 4 + warp] = (double)chi;
             }
         }
     }
