@@ -124,6 +124,63 @@ def test_objective_gradient_parity(ms, oracle_mod, form, ci):
     ctx.close()
 
 
+def _degenerate(N, seed):
+    """A random problem plus visibilities on the degenerate frequencies of the
+    separable forward: the origin (twice), the axes (frac(v dy) = 0, the
+    closed-form column sum's sin(pi b) = 0 branch), exact grid frequencies
+    k / (N dx), the Nyquist edge |u dx| = 1/2, beyond it (aliased), and a whole
+    turn per pixel (u dx = 1).  213 visibilities: ragged tiles."""
+    import dataclasses
+    base = S.random_problem(N, 201, seed, lam=3.0)
+    dx, g = base.dx, 1.0 / (N * base.dx)
+    su = np.array([0, 0, 0.5 / dx, -0.5 / dx, 0.7 / dx, 3 * g, -5 * g, 1.0 / dx, 0.25 / dx, 0, 7 * g, 0])
+    sv = np.array([0, 0.5 / dx, 0, 3 * g, -0.7 / dx, 0, 2 * g, 1.0 / dx, -0.25 / dx, -9 * g, 0, 0])
+    k = su.size
+    rng = np.random.default_rng(seed)
+    return dataclasses.replace(
+        base, name=f"degenerate{N}", u=np.concatenate([su, base.u]), v=np.concatenate([sv, base.v]),
+        vo=np.concatenate([(rng.standard_normal(k) + 1j * rng.standard_normal(k)) * 0.3, base.vo]),
+        sigma=np.concatenate([np.full(k, 0.05), base.sigma]),
+        offsets=np.array([0, k + base.u.size], dtype=np.int64))
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("N,tiling", [(64, None), (256, None), (256, ("resident", 256, 4, 3))])
+def test_degenerate_frequencies(ms, oracle_mod, form, N, tiling):
+    import torch
+    ds = _degenerate(N, 70 + N)
+    ctx = ms.Context(ds, precision=form)
+    if tiling is not None and form in ("bf16x3", "fp16x3"):
+        ctx.set_tiling(*tiling)
+    img = torch.from_numpy(ds.truth).cuda()
+    V = ctx.forward(img).cpu().numpy().astype(np.float64)
+    ref = _oracle_vis(oracle_mod, ds, ds.truth)
+    assert _rel_max(V[:, 0] + 1j * V[:, 1], ref) <= TOL_V[form]
+    phi, chi, Sv, g = ctx.objective_grad(img)
+    P = oracle_mod.Problem.from_dataset(ds)
+    rphi, rchi, rS, rg = oracle_mod.objective_grad(P, ds.truth.astype(np.float64))
+    assert abs(chi - rchi) <= TOL_CHI[form] * abs(rchi)
+    assert _rel_l2(g.cpu().numpy().astype(np.float64), rg) <= TOL_G[form]
+    ctx.close()
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_single_visibility(ms, oracle_mod, form):
+    """Z = 1: one tile holding one visibility, one adjoint unit."""
+    import torch
+    ds = S.random_problem(128, 1, 81, lam=3.0)
+    ctx = ms.Context(ds, precision=form)
+    img = torch.from_numpy(ds.truth).cuda()
+    V = ctx.forward(img).cpu().numpy().astype(np.float64)
+    assert _rel_max(V[:, 0] + 1j * V[:, 1], _oracle_vis(oracle_mod, ds, ds.truth)) <= TOL_V[form]
+    phi, chi, Sv, g = ctx.objective_grad(img)
+    P = oracle_mod.Problem.from_dataset(ds)
+    rphi, rchi, rS, rg = oracle_mod.objective_grad(P, ds.truth.astype(np.float64))
+    assert abs(chi - rchi) <= TOL_CHI[form] * abs(rchi)
+    assert _rel_l2(g.cpu().numpy().astype(np.float64), rg) <= TOL_G[form]
+    ctx.close()
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_host_buffer_entry_matches_device_entry(ms, form):
     import torch

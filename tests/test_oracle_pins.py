@@ -149,6 +149,30 @@ def test_hermitian_symmetry(oracle_mod, form):
 
 
 @pytest.mark.parametrize("form", FORMS)
+def test_degenerate_frequencies_closed_forms(oracle_mod, form):
+    """Eq. 1 on the pixel grid x_m = (m - N/2) dx at frequencies where it has a
+    plain value: the origin gives sum B; u dx = 1/2 gives the alternating sum
+    sum_m (-1)^(m - N/2) B[n, m] (rows likewise for v); a whole turn per pixel
+    (u dx = 1) aliases to u = 0, and any u + 1/dx aliases to u."""
+    N, dx, dy = 32, 2.1e-7, 1.7e-7
+    rng = np.random.default_rng(13)
+    B = rng.random((N, N))
+    sgn = (-1.0) ** (np.arange(N) - N // 2)
+    u0, v0 = 0.31 / dx, -0.22 / dy
+    u = np.array([0.0, 0.5 / dx, 0.0, 0.5 / dx, 1.0 / dx, u0 + 1.0 / dx, u0, -1.5 / dx])
+    v = np.array([0.0, 0.0, 0.5 / dy, -0.5 / dy, 0.0, v0 - 2.0 / dy, v0, 0.0])
+    V = oracle_mod.forward(N, dx, dy, u, v, B, form)
+    scale = B.sum()
+    assert abs(V[0] - B.sum()) <= 1e-13 * scale
+    assert abs(V[1] - (B * sgn[None, :]).sum()) <= 1e-12 * scale
+    assert abs(V[2] - (B * sgn[:, None]).sum()) <= 1e-12 * scale
+    assert abs(V[3] - (B * sgn[:, None] * sgn[None, :]).sum()) <= 1e-12 * scale
+    assert abs(V[4] - V[0]) <= 1e-12 * scale
+    assert abs(V[5] - V[6]) <= 1e-12 * scale
+    assert abs(V[7] - V[1]) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("form", FORMS)
 def test_adjoint_identity(oracle_mod, form):
     """Re<F x, y> = <x, Re(F^H y)> for real x, complex y (Appendix C pairs the
     model's derivative with the chi^2 gradient)."""
