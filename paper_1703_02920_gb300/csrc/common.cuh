@@ -67,6 +67,16 @@ __device__ __forceinline__ float2 df_add(float ah, float al, float bh, float bl)
 // exp(-i * angle) components for the forward sign convention are (c, -s).
 struct cf2 { float x, y; };
 
+// Pixel p of image i from an image source: the caller's FP32 image, or the
+// solver's FP64 state moved along its direction and clipped, max(I + alpha d, G).
+__device__ __forceinline__ double img_value(const ImgSrc& s, int i, int64_t p, int64_t NN) {
+    if (s.f32) return (double)s.f32[(int64_t)i * NN + p];
+    double x = s.f64[(int64_t)i * NN + p];
+    if (s.dir) x = fmax(x + s.alpha[i] * s.dir[(int64_t)i * NN + p], s.G);
+    return x;
+}
+
+
 __device__ __forceinline__ cf2 cmul(cf2 a, cf2 b) {
     return {fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)};
 }

@@ -157,6 +157,11 @@ void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partia
 // ymax (nullable, FP16X3): partials are divided by pow2_scale_for(ymax[0]).
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* unit_off_by_chan_blk,
                           const float* partial, const float* ymax, double* gsum, cudaStream_t st);
+// Unit-partial sum plus gradient assembly in one launch, for images of one
+// channel each (not the shared-image mode).
+void launch_adj_tc_reduce_grad(const DevData& d, const ImgSrc& src, const int* cb_unit_off, const float* partial,
+                               const float* ymax, int projected, float* out32, double* full64, double* proj64,
+                               cudaStream_t st);
 
 // grad_i = sum_{c in image i} A_c * sum_k gsum[k][c] + lambda (1 + log(I/G)); optional projection.
 void launch_finalize(const DevData& d, const ImgSrc& src, const double* gsum, int ks, int projected,

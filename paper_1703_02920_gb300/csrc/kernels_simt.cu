@@ -67,12 +67,6 @@ __device__ __forceinline__ double block_max(double x, double* sh) {
 
 __device__ __forceinline__ int image_of(const DevData& d, int c) { return d.shared ? 0 : c; }
 
-__device__ __forceinline__ double img_value(const ImgSrc& s, int i, int64_t p, int64_t NN) {
-    if (s.f32) return (double)s.f32[(int64_t)i * NN + p];
-    double x = s.f64[(int64_t)i * NN + p];
-    if (s.dir) x = fmax(x + s.alpha[i] * s.dir[(int64_t)i * NN + p], s.G);
-    return x;
-}
 
 // ---------------------------------------------------------------------------
 // a2: attenuation and operand preparation.  B_c = A_c * I.  The BF16x3 form

@@ -462,4 +462,58 @@ void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* cb_
     k_adj_tc_reduce<<<grid, 256, 0, st>>>(d, cb_unit_off, partial, ymax, gsum);
 }
 
+// The unit-partial sum of k_adj_tc_reduce followed directly by the gradient
+// assembly (Eq. chi2gradient with the beam factor, Eq. Sgradient, the positive
+// projection at I = G), for images of one channel each (one image, or a cube):
+// the same arithmetic as the separate reduction and assembly, one launch.
+__global__ void __launch_bounds__(256) k_adj_tc_reduce_grad(DevData d, ImgSrc src,
+                                                            const int* __restrict__ cb_unit_off,
+                                                            const float* __restrict__ partial,
+                                                            const float* __restrict__ ymax, int projected,
+                                                            float* out32, double* full64, double* proj64) {
+    const int N = d.N;
+    const int64_t NN = (int64_t)N * N;
+    const int BLK = N < 256 ? N : 256;
+    const int nbx = N / BLK;
+    const int c = blockIdx.y;  // channel = image
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= NN) return;
+    const int blk = (int)(i / ((int64_t)BLK * BLK));
+    const int64_t loc = i % ((int64_t)BLK * BLK);
+    int nl, ml;
+    adj_partial_rc(loc, BLK, nl, ml);
+    const int64_t p = (int64_t)((blk / nbx) * BLK + nl) * N + (blk % nbx) * BLK + ml;
+    const int cb = c * nbx * nbx + blk;
+    const int u0 = cb_unit_off[cb], u1 = cb_unit_off[cb + 1];
+    const int64_t stride = (int64_t)BLK * BLK;
+    const float* srcp = partial + loc;
+    float s = 0.f, comp = 0.f;
+    int u = u0;
+    for (; u + 8 <= u1; u += 8) {
+        float q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = __ldg(srcp + (int64_t)(u + k) * stride);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) two_sum_acc(s, comp, q[k]);
+    }
+    for (; u < u1; ++u) two_sum_acc(s, comp, __ldg(srcp + (int64_t)u * stride));
+    const double inv = ymax ? 1.0 / (double)pow2_scale_for(ymax[0]) : 1.0;
+    const double gchi = ((double)s + (double)comp) * inv;
+    double g = (double)d.beam[(int64_t)c * NN + p] * gchi;
+    const double x = img_value(src, c, p, NN);
+    if (d.lambda != 0.0) g += d.lambda * (1.0 + log(x / d.G));
+    const double gp = (x <= d.G && g > 0.0) ? 0.0 : g;
+    if (full64) full64[(int64_t)c * NN + p] = g;
+    if (proj64) proj64[(int64_t)c * NN + p] = gp;
+    if (out32) out32[(int64_t)c * NN + p] = (float)(projected ? gp : g);
+}
+
+void launch_adj_tc_reduce_grad(const DevData& d, const ImgSrc& src, const int* cb_unit_off, const float* partial,
+                               const float* ymax, int projected, float* out32, double* full64, double* proj64,
+                               cudaStream_t st) {
+    dim3 grid(prep_blocks(d.N), d.C);
+    k_adj_tc_reduce_grad<<<grid, 256, 0, st>>>(d, src, cb_unit_off, partial, ymax, projected, out32, full64,
+                                                proj64);
+}
+
 }  // namespace msk
