@@ -197,6 +197,14 @@ mem_status mem_forward_gridded(mem_ctx *ctx, const float *image_dev, int32_t pad
  * adjoint in its precision form.  out_dev: device, C x N x N float32. */
 mem_status mem_dirty_image(mem_ctx *ctx, int32_t psf, float *out_dev);
 
+/* Residual map: the natural-weights dirty image (as mem_dirty_image) of the
+ * residual visibilities V°_k - V_k(I), with V(I) the forward operator (Eq. 1)
+ * of the model image in the context's precision form.  After a solve it shows
+ * what the model leaves unexplained.  image_dev: device, n_images x N x N
+ * float32 (the image before the primary beam); out_dev: device, C x N x N
+ * float32. */
+mem_status mem_residual_image(mem_ctx *ctx, const float *image_dev, float *out_dev);
+
 /* Mosaics (Section 2.4: one attenuation image per pointing, centred on its
  * field).  A pointing whose phase-tracking centre lies at (x_p, y_p)
  * (radians, relative to the image's phase centre, pixel (N/2, N/2)) measures

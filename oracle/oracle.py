@@ -490,19 +490,22 @@ def mosaic_forward(N: int, dx: float, dy: float, u, v, A_p, I, x_p: float, y_p: 
     return forward(N, dx, dy, u, v, B) * np.exp(2j * np.pi * (u * x_p + v * y_p))
 
 
-def dirty_image(P: Problem, psf: bool = False) -> np.ndarray:
+def dirty_image(P: Problem, psf: bool = False, vis=None) -> np.ndarray:
     """Natural-weights dirty image per channel (Appendix A, Eq. dirty, with the
     measured visibilities in place of gridded ones), or the PSF (Eq. PSF):
     I^D(X) = sum_k omega_k Re(V_k exp(+2 pi i U_k . X)), omega_k = w_k / sum_l w_l
-    over the channel's samples; no primary-beam factor.  (C, N, N)."""
+    over the channel's samples; no primary-beam factor.  (C, N, N).  vis: other
+    visibilities in place of the measured ones (the residuals V° - V for a
+    residual map)."""
     out = np.zeros((P.C, P.N, P.N))
+    vo = P.vo if vis is None else np.asarray(vis, dtype=np.complex128)
     for c in range(P.C):
         s = P.sl(c)
         w = P.weights(c)
         if w.size == 0:
             continue
         om = w / np.sum(w)
-        y = om * (np.ones(w.size) if psf else P.vo[s])
+        y = om * (np.ones(w.size) if psf else vo[s])
         out[c] = adjoint(P.N, P.dx, P.dy, P.u[s], P.v[s], y.astype(np.complex128))
     return out
 

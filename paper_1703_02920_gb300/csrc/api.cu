@@ -1122,17 +1122,18 @@ mem_status mem_forward_gridded(mem_ctx* c, const float* image_dev, int32_t pad, 
     return after_launch(c, "gridded forward: interpolation");
 }
 
-mem_status mem_dirty_image(mem_ctx* c, int32_t psf, float* out_dev) {
-    if (!c || !out_dev) return fail(c, MEM_EINVAL, "null argument");
-    TRY(ensure_buffers(c));
+namespace {
+// Shared by the dirty image, the PSF and the residual map: natural weights
+// times the chosen visibilities (already in y32 / y64 for residuals), then the
+// adjoint without the beam factor.
+mem_status dirty_from(mem_ctx* c, int what, float* out_dev) {
     if (!c->wsum) {
         TRY(dalloc(c, &c->wsum, (size_t)c->C));
         CK(cudaMemcpyAsync(c->wsum, c->wsum_h.data(), c->C * sizeof(double), cudaMemcpyHostToDevice, c->st),
            "weight sums");
     }
     DevData d = c->dd();
-    launch_dirty_y(d, c->wsum, psf ? 1 : 0, c->Z, c->y32, c->prec == MEM_PREC_FP64_DIRECT ? c->y64 : nullptr,
-                   c->st);
+    launch_dirty_y(d, c->wsum, what, c->Z, c->y32, c->prec == MEM_PREC_FP64_DIRECT ? c->y64 : nullptr, c->st);
     if (c->Z > 0) c->launches++;
     TRY(after_launch(c, "dirty image weights"));
     int ks = 1;
@@ -1140,6 +1141,22 @@ mem_status mem_dirty_image(mem_ctx* c, int32_t psf, float* out_dev) {
     launch_dirty_out(d, c->gsum, ks, out_dev, c->st);
     c->launches++;
     return after_launch(c, "dirty image");
+}
+}  // namespace
+
+mem_status mem_dirty_image(mem_ctx* c, int32_t psf, float* out_dev) {
+    if (!c || !out_dev) return fail(c, MEM_EINVAL, "null argument");
+    TRY(ensure_buffers(c));
+    return dirty_from(c, psf ? 1 : 0, out_dev);
+}
+
+mem_status mem_residual_image(mem_ctx* c, const float* image_dev, float* out_dev) {
+    if (!c || !out_dev || !image_dev) return fail(c, MEM_EINVAL, "null argument");
+    TRY(ensure_buffers(c));
+    ImgSrc src{image_dev, nullptr, nullptr, nullptr, c->G, 0};
+    void* model = c->prec == MEM_PREC_FP64_DIRECT ? (void*)c->y64 : (void*)c->y32;
+    TRY(run_forward(c, src, FWD_VIS, false, model));
+    return dirty_from(c, 2, out_dev);
 }
 
 mem_status mem_phase_rotate(int64_t n_vis, const double* u, const double* v, double x_p, double y_p,

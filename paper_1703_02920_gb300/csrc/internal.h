@@ -123,9 +123,10 @@ int fwd_rs_smem_bytes(int N, int stages);
 // The paper's gridded forward: padding (M = pad N, image centred) and the
 // modulated bilinear interpolation of the batched R2C half spectra.
 void launch_grid_pad(const DevData& d, const float* img, int M, float* P, cudaStream_t st);
-// Dirty image / PSF: weighted adjoint inputs, and the per-channel image from
-// the adjoint's FP64 sums (no primary-beam factor).
-void launch_dirty_y(const DevData& d, const double* wsum, int psf, int64_t z_total, float2* y32, double2* y64,
+// Dirty image / PSF / residual map: weighted adjoint inputs (what: 0 data,
+// 1 PSF, 2 residuals against the model in y32 / y64), and the per-channel
+// image from the adjoint's FP64 sums (no primary-beam factor).
+void launch_dirty_y(const DevData& d, const double* wsum, int what, int64_t z_total, float2* y32, double2* y64,
                     cudaStream_t st);
 void launch_dirty_out(const DevData& d, const double* gsum, int ks, float* out, cudaStream_t st);
 void launch_grid_interp(const DevData& d, int M, const void* F, int64_t z_total, float2* vis, cudaStream_t st);

@@ -687,7 +687,9 @@ namespace msk {
 // y_k = omega_k V_k (or omega_k), omega_k = w_k / (sum of w over the channel);
 // the sum of the adjoint's splits per channel, without the primary beam.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_dirty_y(DevData d, const double* __restrict__ wsum, int psf,
+// what: 0 measured visibilities, 1 PSF (V = 1), 2 residuals V° - V, with the
+// model V read from y64 (FP64 form) or y32 at the same index it overwrites.
+__global__ void __launch_bounds__(256) k_dirty_y(DevData d, const double* __restrict__ wsum, int what,
                                                  int64_t z_total, float2* __restrict__ y32,
                                                  double2* __restrict__ y64) {
     const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
@@ -699,7 +701,12 @@ __global__ void __launch_bounds__(256) k_dirty_y(DevData d, const double* __rest
         else hi = mid;
     }
     const double om = d.w[j] / wsum[lo];
-    const double2 v = psf ? make_double2(1.0, 0.0) : d.vo[j];
+    double2 v = what == 1 ? make_double2(1.0, 0.0) : d.vo[j];
+    if (what == 2) {
+        const double2 m = y64 ? y64[j] : make_double2((double)y32[j].x, (double)y32[j].y);
+        v.x -= m.x;
+        v.y -= m.y;
+    }
     y32[j] = make_float2((float)(om * v.x), (float)(om * v.y));
     if (y64) y64[j] = make_double2(om * v.x, om * v.y);
 }
@@ -715,10 +722,10 @@ __global__ void __launch_bounds__(256) k_dirty_out(DevData d, const double* __re
     out[(int64_t)c * NN + p] = (float)s;
 }
 
-void launch_dirty_y(const DevData& d, const double* wsum, int psf, int64_t z_total, float2* y32, double2* y64,
+void launch_dirty_y(const DevData& d, const double* wsum, int what, int64_t z_total, float2* y32, double2* y64,
                     cudaStream_t st) {
     if (z_total <= 0) return;
-    k_dirty_y<<<(unsigned)((z_total + 255) / 256), 256, 0, st>>>(d, wsum, psf, z_total, y32, y64);
+    k_dirty_y<<<(unsigned)((z_total + 255) / 256), 256, 0, st>>>(d, wsum, what, z_total, y32, y64);
 }
 
 void launch_dirty_out(const DevData& d, const double* gsum, int ks, float* out, cudaStream_t st) {

@@ -72,7 +72,7 @@ EXPORTS = ["mem_create", "mem_destroy", "mem_last_error", "mem_status_string", "
            "mem_objective_grad_host", "mem_scalars_dev", "mem_solve", "mem_sync", "mem_launch_count",
            "mem_profile", "mem_profile_read", "mem_adjoint_noalloc", "mem_use_graphs", "mem_autotune",
            "mem_set_tiling", "mem_tiling", "mem_forward_gridded",
-           "mem_dirty_image", "mem_beam_fit", "mem_phase_rotate"]
+           "mem_dirty_image", "mem_residual_image", "mem_beam_fit", "mem_phase_rotate"]
 
 
 def library_path() -> str:
@@ -136,6 +136,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.mem_forward_gridded.restype = ctypes.c_int
     lib.mem_dirty_image.argtypes = [P, I32, P]
     lib.mem_dirty_image.restype = ctypes.c_int
+    lib.mem_residual_image.argtypes = [P, P, P]
+    lib.mem_residual_image.restype = ctypes.c_int
     lib.mem_beam_fit.argtypes = [P, I32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     lib.mem_beam_fit.restype = ctypes.c_int
     lib.mem_phase_rotate.argtypes = [ctypes.c_int64, P, P, ctypes.c_double, ctypes.c_double, P]
@@ -274,6 +276,10 @@ def mem_dirty_image(ctx, psf: bool, out_dev):
     _check(load().mem_dirty_image(ctx, int(bool(psf)), _ptr(out_dev)), ctx)
 
 
+def mem_residual_image(ctx, image_dev, out_dev):
+    _check(load().mem_residual_image(ctx, _ptr(image_dev), _ptr(out_dev)), ctx)
+
+
 def mem_beam_fit(psf, dx: float, dy: float):
     """(BMAJ, BMIN, BPA, beam area in pixels) of a host PSF image (n x n float32)."""
     import numpy as np
@@ -385,6 +391,12 @@ class Context:
         """Natural-weights dirty image (or PSF) per channel, (C, N, N) float32."""
         out = self.torch.empty((self.C, self.N, self.N), dtype=self.torch.float32, device="cuda")
         mem_dirty_image(self.handle, psf, out)
+        return out
+
+    def residual_image(self, image):
+        """Natural-weights dirty image of V° - V(image) per channel, (C, N, N) float32."""
+        out = self.torch.empty((self.C, self.N, self.N), dtype=self.torch.float32, device="cuda")
+        mem_residual_image(self.handle, self._img(image), out)
         return out
 
     def adjoint(self, y):

@@ -1,5 +1,6 @@
-"""Natural-weights dirty image and PSF (Appendix A) on the GPU, per channel
-and form, against the oracle; the PSF peaks at 1 on the phase centre."""
+"""Natural-weights dirty image, PSF and residual map (Appendix A) on the GPU,
+per channel and form, against the oracle; the PSF peaks at 1 on the phase
+centre."""
 import numpy as np
 import pytest
 
@@ -34,6 +35,31 @@ def test_dirty_image_and_psf_match_oracle(ms, oracle_mod, form):
         if psf:
             assert got[0][64, 64] == pytest.approx(1.0, abs=1e-5)
     ctx.close()
+
+
+@pytest.mark.parametrize("form", list(TOL))
+def test_residual_map_matches_oracle(ms, oracle_mod, form):
+    """Dirty image of V° - V(I): the oracle's dirty image of its own residuals;
+    a model equal to the data leaves an empty map."""
+    import dataclasses
+    ds = S.random_problem(128, 0, 96, C=3, z_list=[900, 0, 512])
+    P = oracle_mod.Problem.from_dataset(ds)
+    img = ds.truth.astype(np.float64)
+    V = np.concatenate(oracle_mod.model_vis(P, img))
+    ctx = ms.Context(ds, precision=form)
+    got = ctx.residual_image(ds.truth).cpu().numpy().astype(np.float64)
+    ctx.close()
+    ref = oracle_mod.dirty_image(P, vis=P.vo - V)
+    for c in (0, 2):
+        assert np.linalg.norm(got[c] - ref[c]) / np.linalg.norm(ref[c]) <= TOL[form], c
+    assert np.all(got[1] == 0)  # the empty channel
+    # data = model: only the forward's rounding remains
+    exact = dataclasses.replace(ds, vo=V)
+    ctx = ms.Context(exact, precision=form)
+    zero = ctx.residual_image(ds.truth).cpu().numpy().astype(np.float64)
+    ctx.close()
+    dirty = oracle_mod.dirty_image(oracle_mod.Problem.from_dataset(exact))
+    assert np.max(np.abs(zero)) <= 10 * TOL[form] * np.max(np.abs(dirty))
 
 
 def test_config1_beam_from_gpu_psf(ms, oracle_mod):
