@@ -135,9 +135,17 @@ def job_value(units: int, world: int, ms_step: float) -> float:
     return units * world / (ms_step * 1e-3)
 
 
-def make_data(config: int):
+def make_data(config: int, shared_image: bool = False):
+    """The config's synthetic data set; shared_image: one image for all its
+    channels (the multi-frequency mode of Eq. chi2-multi), the channel mean of
+    the cube as its stand-in sky."""
+    import dataclasses
     from paper_1703_02920_gb300 import synth
-    return synth.make(config)
+    ds = synth.make(config)
+    if shared_image:
+        ds = dataclasses.replace(ds, shared_image=True,
+                                 truth=np.mean(ds.truth, axis=0, keepdims=True).astype(np.float32))
+    return ds
 
 
 def cpu_baseline(ds, budget_s: float = 12.0):
@@ -174,7 +182,7 @@ def cpu_baseline(ds, budget_s: float = 12.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    ds = make_data(args.config)
+    ds = make_data(args.config, args.shared_image)
     import oracle
     oracle.build()
     per = []
@@ -188,7 +196,9 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.config], "precision": "fp64 oracle (CPU)"},
+            "config": {"workload": WORKLOADS[args.config] + (
+                ", one image shared by all channels (Eq. chi2-multi)" if args.shared_image else ""),
+                "precision": "fp64 oracle (CPU)"},
             "cpu_baseline": dict(info, value=value),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -211,6 +221,8 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="only W + K objective+gradient evaluations with the default tiling (for ncu captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shared-image", action="store_true",
+                    help="one image for all channels (multi-frequency mode); meaningful for the cube config 4")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -231,7 +243,7 @@ def main():
     from paper_1703_02920_gb300 import memsynth
 
     memsynth.load()
-    ds = make_data(args.config)
+    ds = make_data(args.config, args.shared_image)
     N, Z = ds.N, ds.Z
     units = Z * N * N
     ctx = memsynth.Context(ds, precision=args.precision)
@@ -403,7 +415,9 @@ def main():
                 "vs_baseline": None,
                 "dtype": {"bf16x3": "bf16x3", "fp16x3": "f16x3", "fp32_direct": "f32", "fp64_direct": "f64"}[args.precision],
                 "data": "synthetic",
-                "config": {"workload": WORKLOADS[args.config], "precision": args.precision,
+                "config": {"workload": WORKLOADS[args.config] + (
+                               ", one image shared by all channels (Eq. chi2-multi)" if args.shared_image else ""),
+                           "precision": args.precision,
                            "image": f"{N}x{N}", "visibilities": Z, "parallelism": f"replicas x{world}",
                            "l2": "flushed between timed steps (256 MB write)", "tiles": tiles},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(img.numel() * 4),

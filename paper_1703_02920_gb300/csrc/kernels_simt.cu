@@ -207,6 +207,9 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
     const int c = blockIdx.y;
     const int i = image_of(d, c);
     const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    // the entropy partial of an image is formed by its first channel only
+    // (the others would repeat it in the shared-image mode)
+    const bool ent = ent_part && !(d.shared && c != 0);
     double e = 0.0;
     if (p < NN) {
         double x = img_value(src, i, p, NN);
@@ -217,8 +220,8 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
             // change of sum x log(x/G)
             const double x0 = src.f64[(int64_t)i * NN + p];
             xb = x - x0;
-            if (ent_part) e = x * log(x / src.G) - x0 * log(x0 / src.G);
-        } else if (ent_part) {
+            if (ent) e = x * log(x / src.G) - x0 * log(x0 / src.G);
+        } else if (ent) {
             e = x * log(x / src.G);
         }
         double b = (double)d.beam[(int64_t)c * NN + p] * xb;
@@ -250,10 +253,9 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
             }
         }
     }
-    if (ent_part) {
-        bool owner = d.shared ? (c == 0) : true;
+    if (ent) {  // uniform over the block (one channel per block row)
         double s = block_sum<256>(e, sh);
-        if (owner && threadIdx.x == 0) ent_part[(int64_t)i * gridDim.x + blockIdx.x] = -s;
+        if (threadIdx.x == 0) ent_part[(int64_t)i * gridDim.x + blockIdx.x] = -s;
     }
 }
 

@@ -466,6 +466,9 @@ void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* cb_
 // assembly (Eq. chi2gradient with the beam factor, Eq. Sgradient, the positive
 // projection at I = G), for images of one channel each (one image, or a cube):
 // the same arithmetic as the separate reduction and assembly, one launch.
+// log(I/G) stays FP64: with an FP32 log the 50-iteration solve of the
+// 64x64 problem ended 1.4e-3 (relative L2) from the oracle's image in the
+// BF16X3 form, against 4.6e-4.
 __global__ void __launch_bounds__(256) k_adj_tc_reduce_grad(DevData d, ImgSrc src,
                                                             const int* __restrict__ cb_unit_off,
                                                             const float* __restrict__ partial,
