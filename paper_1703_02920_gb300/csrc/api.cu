@@ -279,11 +279,6 @@ struct mem_ctx {
     float2* y32 = nullptr;
     double2* y64 = nullptr;
     double *chi_part = nullptr, *ent_part = nullptr, *gsum = nullptr, *scal = nullptr, *img_tmp = nullptr;
-    // side stream for the scalar reduction, which overlaps the adjoint (fork
-    // after the forward, join before the evaluation returns)
-    cudaStream_t side_st = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    bool scal_side = false, scal_pending = false;
     int gsum_ks = 0;
     float* bf32 = nullptr;
     double* bf64 = nullptr;
@@ -646,20 +641,9 @@ mem_status run_forward(mem_ctx* c, const ImgSrc& src, int mode, bool entropy, vo
     if ((tc ? c->n_tiles_tc : c->n_tiles) > 0) c->launches++;
     TRY(after_launch(c, "forward kernel"));
     if (mode != FWD_VIS) {
-        if (c->scal_side && !c->profiling) {
-            // the reduction reads only the forward's and the prep's partials:
-            // run it beside whatever the stream does next
-            CK(cudaEventRecord(c->ev_fork, c->st), "fork");
-            CK(cudaStreamWaitEvent(c->side_st, c->ev_fork, 0), "fork");
-            launch_scalars(d, tc ? c->tile_off_tc : c->tile_off, c->chi_part, c->ent_part, entropy ? 1 : 0,
-                           c->scal, c->img_tmp, c->side_st);
-            CK(cudaEventRecord(c->ev_join, c->side_st), "join");
-            c->scal_pending = true;
-        } else {
-            KTimer t(c, "scalars");
-            launch_scalars(d, tc ? c->tile_off_tc : c->tile_off, c->chi_part, c->ent_part, entropy ? 1 : 0,
-                           c->scal, c->img_tmp, c->st);
-        }
+        KTimer t(c, "scalars");
+        launch_scalars(d, tc ? c->tile_off_tc : c->tile_off, c->chi_part, c->ent_part, entropy ? 1 : 0,
+                       c->scal, c->img_tmp, c->st);
         c->launches++;
         TRY(after_launch(c, "scalar reduction"));
     }
@@ -709,39 +693,21 @@ mem_status run_objgrad(mem_ctx* c, const ImgSrc& src, int projected, float* out3
                        double* proj64) {
     TRY(ensure_buffers(c));
     void* yout = c->prec == MEM_PREC_FP64_DIRECT ? (void*)c->y64 : (void*)c->y32;
-    c->scal_side = true;
-    const mem_status sf = run_forward(c, src, FWD_RESID, true, yout);
-    c->scal_side = false;
-    auto join = [&]() -> mem_status {
-        if (!c->scal_pending) return MEM_OK;
-        c->scal_pending = false;
-        CK(cudaStreamWaitEvent(c->st, c->ev_join, 0), "join");
-        return MEM_OK;
-    };
-    if (sf != MEM_OK) {
-        join();
-        return sf;
-    }
+    TRY(run_forward(c, src, FWD_RESID, true, yout));
     int ks = 1;
     // images of one channel each: the adjoint's unit-partial sum and the
     // gradient assembly are one launch
     const bool fused = is_tc(c->prec) && !c->shared;
-    mem_status sa = run_adjoint(c, &ks, true, !fused);
-    if (sa == MEM_OK) {
-        if (fused) {
-            KTimer t(c, "adj_reduce_grad");
-            launch_adj_tc_reduce_grad(c->dd(), src, c->cb_off, c->partial,
-                                      c->prec == MEM_PREC_FP16X3 ? c->ymax : nullptr, projected, out32, full64,
-                                      proj64, c->st);
-        } else {
-            KTimer t(c, "finalize");
-            launch_finalize(c->dd(), src, c->gsum, ks, projected, out32, full64, proj64, c->st);
-        }
-        c->launches++;
+    TRY(run_adjoint(c, &ks, true, !fused));
+    if (fused) {
+        KTimer t(c, "adj_reduce_grad");
+        launch_adj_tc_reduce_grad(c->dd(), src, c->cb_off, c->partial, c->prec == MEM_PREC_FP16X3 ? c->ymax : nullptr,
+                                  projected, out32, full64, proj64, c->st);
+    } else {
+        KTimer t(c, "finalize");
+        launch_finalize(c->dd(), src, c->gsum, ks, projected, out32, full64, proj64, c->st);
     }
-    const mem_status sj = join();
-    if (sa != MEM_OK) return sa;
-    if (sj != MEM_OK) return sj;
+    c->launches++;
     return after_launch(c, "gradient assembly");
 }
 
@@ -1253,12 +1219,8 @@ mem_status mem_use_graphs(mem_ctx* c, int32_t enable) {
 void mem_destroy(mem_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->st);
-    if (c->side_st) cudaStreamSynchronize(c->side_st);
     drop_graphs(c);
     if (c->cap_st) cudaStreamDestroy(c->cap_st);
-    if (c->side_st) cudaStreamDestroy(c->side_st);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (auto& k : c->kev) {
         cudaEventDestroy(k.a);
         cudaEventDestroy(k.b);
@@ -1385,14 +1347,6 @@ mem_status mem_create(const mem_config* cfg, const double* u, const double* v, c
     }
     launch_phase_prep(Z, c->u, c->v, c->dx, c->dy, c->pa, c->pb, c->st);
     c->launches++;
-    e = cudaStreamCreateWithFlags(&c->side_st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-        cuda_fail(c, e, "side stream");
-        g_last_error = c->err;
-        return bail(MEM_ECUDA);
-    }
 
     build_tiles(c, 128, c->tiles_h, c->tile_off_h);
     build_tiles(c, TC_TILE, c->tiles_tc_h, c->tile_off_tc_h);
