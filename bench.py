@@ -193,8 +193,11 @@ def run_reference(args, rank, world):
             per.append(b["value"])
             info = b
     value = statistics.mean(per)
+    # one step of the full workload at the sampled rate (each timed step is a
+    # bounded sample of it; see cpu_baseline.sample)
+    ms_full = ds.Z * ds.N * ds.N / value * 1e3 if value > 0 else None
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_full, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.config] + (
                 ", one image shared by all channels (Eq. chi2-multi)" if args.shared_image else ""),
