@@ -110,7 +110,11 @@ typedef struct {
  * doubles, interleaved re/im), sigma (Z doubles, > 0) and pb (C*N*N floats)
  * to the device, prepares per-visibility phase increments (FP64 reduction of
  * u dx, v dy to 64-bit fixed-point turns) and binds the context to `stream`
- * (a cudaStream_t; NULL = legacy default stream).  All host pointers. */
+ * (a cudaStream_t; NULL = legacy default stream).  All host pointers.
+ * Resident device data: 84 bytes per visibility (u, v, the fixed-point
+ * phases, V° in FP64 and as FP32 hi/lo pairs, 1/sigma^2 in FP64 and FP32, the
+ * weighted residual) and 4 bytes per beam pixel; the first evaluation adds
+ * work buffers (operand planes, split-K partials: about 40 MB at N = 256). */
 mem_status mem_create(const mem_config *cfg, const double *u, const double *v,
                       const double *vis_obs, const double *sigma, const float *pb,
                       void *stream, mem_ctx **out);
