@@ -208,6 +208,45 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_sweep(args):
+    """Evaluation rate over image size and visibility count on seeded random
+    problems (one JSON line per size); L2 flushed between evaluations, median
+    of CUDA-event times on the library's stream, autotuned tiling."""
+    import torch
+    from paper_1703_02920_gb300 import memsynth, synth
+    torch.cuda.set_device(0)
+    memsynth.load()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for N in (128, 256, 512, 1024):
+        for Z in (100_000, 1_000_000, 10_000_000):
+            ds = synth.random_problem(N, Z, 11, lam=3.0)
+            ctx = memsynth.Context(ds, precision=args.precision)
+            img = torch.from_numpy(ds.truth).cuda()
+            g = torch.empty_like(img)
+            if args.precision in ("bf16x3", "fp16x3"):
+                ctx.autotune(img, reps=2)
+            for _ in range(3):
+                memsynth.mem_objective_grad(ctx.handle, img, g, 0, want_scalars=False)
+            steps = max(3, min(50, int(2e13 / (Z * N * N)) + 3))
+            ts = []
+            for _ in range(steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(ctx.stream)
+                memsynth.mem_objective_grad(ctx.handle, img, g, 0, want_scalars=False)
+                b.record(ctx.stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            t = float(np.median(ts))
+            print(json.dumps({"sweep": True, "precision": args.precision, "N": N, "visibilities": Z,
+                              "ms_per_evaluation": t, "value": Z * N * N / (t * 1e-3), "unit": UNIT,
+                              "tiling": list(ctx.tiling()) if args.precision in ("bf16x3", "fp16x3") else None}),
+                  flush=True)
+            ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,8 +265,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shared-image", action="store_true",
                     help="one image for all channels (multi-frequency mode); meaningful for the cube config 4")
+    ap.add_argument("--sweep", action="store_true",
+                    help="evaluation rate over N in 128..1024 and 1e5..1e7 visibilities (one line per size)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.sweep:
+        return run_sweep(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
