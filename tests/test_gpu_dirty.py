@@ -37,12 +37,14 @@ def test_dirty_image_and_psf_match_oracle(ms, oracle_mod, form):
     ctx.close()
 
 
+@pytest.mark.parametrize("shared", [False, True])
 @pytest.mark.parametrize("form", list(TOL))
-def test_residual_map_matches_oracle(ms, oracle_mod, form):
-    """Dirty image of V° - V(I): the oracle's dirty image of its own residuals;
+def test_residual_map_matches_oracle(ms, oracle_mod, form, shared):
+    """Dirty image of V° - V(I): the oracle's dirty image of its own residuals
+    (per channel; one model image for all channels in the shared-image mode);
     a model equal to the data leaves an empty map."""
     import dataclasses
-    ds = S.random_problem(128, 0, 96, C=3, z_list=[900, 0, 512])
+    ds = S.random_problem(128, 0, 96, C=3, z_list=[900, 0, 512], shared_image=shared)
     P = oracle_mod.Problem.from_dataset(ds)
     img = ds.truth.astype(np.float64)
     V = np.concatenate(oracle_mod.model_vis(P, img))
