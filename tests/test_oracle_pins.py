@@ -371,6 +371,133 @@ def test_polish_is_continuous_in_the_start(oracle_mod):
     assert abs(a - b) <= 2e-5 * xs
 
 
+def test_polish_is_exact_on_a_parabola_and_stays_in_its_window(oracle_mod):
+    """The central-difference Newton step lands on a parabola's vertex from any
+    start within h of it, and never leaves [x - h, x + h] (it is a clamped
+    step, so a vertex farther away is approached by h only)."""
+    f = lambda t: 3.0 * (t - 1.7) ** 2 - 2.0
+    for x in (1.55, 1.7, 1.84):
+        assert abs(oracle_mod.polish(f, x, f(x), 0.2) - 1.7) <= 1e-12
+    assert oracle_mod.polish(f, 1.0, f(1.0), 0.2) == pytest.approx(1.2, abs=1e-15)
+    assert oracle_mod.polish(f, 2.5, f(2.5), 0.2) == pytest.approx(2.3, abs=1e-15)
+    # no curvature (a line, or a concave stencil): the step stays where it is
+    assert oracle_mod.polish(lambda t: -t, 0.8, -0.8, 0.1) == 0.8
+    assert oracle_mod.polish(lambda t: -(t - 1) ** 2, 0.8, -0.04, 0.1) == 0.8
+
+
+def test_projection_rules(oracle_mod):
+    """Positive projection at the bound I = G (Eq. minproblem): a pixel on the
+    bound keeps a gradient component only if descent (-g) raises it, and a
+    search direction only if it does not lower it.  Pixels above the bound
+    are never touched."""
+    G = 1e-3
+    I = np.array([G, G, 2 * G, 3 * G, G, 0.5 * G])
+    g = np.array([1.0, -1.0, 1.0, -1.0, 0.0, 2.0])
+    assert np.array_equal(oracle_mod.project_grad(I, g, G), [0.0, -1.0, 1.0, -1.0, 0.0, 0.0])
+    d = np.array([-1.0, 1.0, -1.0, 1.0, 0.0, -3.0])
+    assert np.array_equal(oracle_mod.project_dir(I, d, G), [0.0, 1.0, -1.0, 1.0, 0.0, 0.0])
+    # the inputs are not modified in place
+    assert np.array_equal(g, [1.0, -1.0, 1.0, -1.0, 0.0, 2.0])
+    assert np.array_equal(d, [-1.0, 1.0, -1.0, 1.0, 0.0, -3.0])
+
+
+def test_cg_terminates_on_a_quadratic(oracle_mod):
+    """With lambda = 0 and the bound inactive Phi = chi^2 is a convex quadratic
+    in n = N^2 unknowns.  Polak-Ribiere CG with an exact line search is then
+    linear CG, which reaches the minimiser in at most n steps in exact
+    arithmetic (Hestenes and Stiefel 1952); the line search is exact here
+    because the first trial step is the quadratic model's minimiser and the
+    final Newton step is exact on a parabola.  Steepest descent (beta = 0), a
+    wrong sign of beta or of the direction update stall far above it."""
+    N = 4
+    ds = S.random_problem(N, 40, 31, C=1, shared_image=False, lam=0.0, G=1e-12)
+    P = oracle_mod.Problem.from_dataset(ds)
+    rng = np.random.default_rng(5)
+    truth = 1.0 + rng.random((1, N, N))
+    P.vo = oracle_mod.model_vis(P, truth)[0]
+    I0 = truth + 0.3 * rng.standard_normal((1, N, N))
+    assert I0.min() > 0.5
+    img, hists = oracle_mod.solve(P, I0, N * N + 4)
+    phis = [h["phi"] for h in hists[0]]
+    assert np.max(np.abs(img - truth)) <= 1e-9
+    assert phis[-1] <= 1e-15 * phis[0]
+    # after n steps only rounding is left (a factor 1e6 below the start at least)
+    assert phis[min(N * N, len(phis) - 1)] <= 1e-5 * phis[0]
+
+
+@pytest.mark.parametrize("lam", [50.0, 2.0])
+def test_solver_reaches_bounded_minimiser(oracle_mod, lam):
+    """For lambda > 0 Phi is strictly convex on I >= G (quadratic chi^2 plus
+    I log I), so the minimiser of Eq. minproblem is unique: the projected CG
+    lands on the point scipy's L-BFGS-B finds with the same bounds, Phi never
+    increases, every iterate stays feasible and the bound-constrained KKT
+    residual falls by 1e3 at least."""
+    from scipy.optimize import minimize
+    ds = _tiny_problem(seed=21, N=8, Z=60, lam=lam)
+    P = oracle_mod.Problem.from_dataset(ds)
+    I0 = np.full((1, 8, 8), P.G)
+    img, hists = oracle_mod.solve(P, I0, 150)
+    phis = [h["phi"] for h in hists[0]]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(phis, phis[1:]))
+    assert img.min() >= P.G
+    # the bound is active somewhere, so the projection is exercised
+    assert np.count_nonzero(img <= P.G) > 0
+
+    def fg(x):
+        phi, _, _, g = oracle_mod.objective_grad(P, x.reshape(1, 8, 8))
+        return phi, g.ravel()
+
+    ref = minimize(fg, np.full(64, 2 * P.G), jac=True, method="L-BFGS-B",
+                   bounds=[(P.G, None)] * 64, options=dict(maxiter=5000, ftol=1e-15, gtol=1e-12))
+    rel = np.linalg.norm(img.ravel() - ref.x) / np.linalg.norm(ref.x)
+    assert rel < 1e-3, rel
+    assert phis[-1] <= ref.fun * (1 + 1e-12)
+    _, _, _, g = oracle_mod.objective_grad(P, img)
+    k_end = oracle_mod.kkt_residual(img, g, P.G)
+    _, _, _, g0 = oracle_mod.objective_grad(P, np.maximum(I0, P.G))
+    assert k_end < 1e-3 * oracle_mod.kkt_residual(np.maximum(I0, P.G), g0, P.G)
+
+
+def test_shared_image_solve_reaches_the_summed_minimiser(oracle_mod):
+    """Shared-image mode (Eq. chi2-multi): one image, chi^2 summed over the
+    channels, each with its own beam.  The solve lands on L-BFGS-B's bounded
+    minimiser of that summed objective."""
+    from scipy.optimize import minimize
+    ds = _tiny_problem(seed=23, N=8, Z=30, C=3, shared=True, lam=20.0)
+    P = oracle_mod.Problem.from_dataset(ds)
+    assert P.shared_image and P.C == 3
+    I0 = np.full((1, 8, 8), P.G)
+    img, hists = oracle_mod.solve(P, I0, 150)
+    assert img.shape == (1, 8, 8) and len(hists) == 1
+
+    def fg(x):
+        phi, _, _, g = oracle_mod.objective_grad(P, x.reshape(1, 8, 8))
+        return phi, g.ravel()
+
+    ref = minimize(fg, np.full(64, 2 * P.G), jac=True, method="L-BFGS-B",
+                   bounds=[(P.G, None)] * 64, options=dict(maxiter=5000, ftol=1e-15, gtol=1e-12))
+    rel = np.linalg.norm(img.ravel() - ref.x) / np.linalg.norm(ref.x)
+    assert rel < 1e-3, rel
+
+
+def test_cube_mode_solves_channels_independently(oracle_mod):
+    """Cube mode (independent channel images): solving the cube equals solving
+    each channel alone, bit for bit."""
+    ds = _tiny_problem(seed=22, C=2, N=8, Z=40, lam=20.0)
+    P = oracle_mod.Problem.from_dataset(ds)
+    assert not P.shared_image
+    I0 = np.full((2, 8, 8), P.G)
+    imgs, _ = oracle_mod.solve(P, I0, 10)
+    for c in range(2):
+        s = P.sl(c)
+        Pc = oracle_mod.Problem(P.N, P.dx, P.dy, P.u[s], P.v[s], P.vo[s], P.sigma[s], P.pb[c:c + 1],
+                                np.array([0, s.stop - s.start]), P.G, P.lam)
+        ic, _ = oracle_mod.solve(Pc, I0[c:c + 1], 10)
+        assert np.array_equal(ic[0], imgs[c])
+    # and the two channels really differ (their data do)
+    assert not np.array_equal(imgs[0], imgs[1])
+
+
 # ---------------------------------------------------------------------------
 # the paper's gridded forward (Section 2.4 steps, Algorithm alg:chi2gpu)
 # ---------------------------------------------------------------------------
