@@ -7,15 +7,20 @@ metric is vis*pixel/s = Z * N^2 * steps / s.  Default workload: the
 256 x 256, 999,600-visibility single-channel data set (50 antennas, 1 km
 disk, 816 Earth-rotation dumps), split-FP16 (3-term) tensor-core form, tile
 shapes picked by the library's autotuner before the timed region.  Beside
-it: a fixed-iteration MEM solve timed in the same form and in the FP64
-direct form.
+it, in the same JSON line: the same evaluation on the largest single-image
+workload (1024 x 1024, 2.0e7 visibilities) with its own roofline, a
+fixed-iteration MEM solve timed in the same form and in the FP64 direct
+form, the paper's gridded forward, and the FP64 oracle on the host cores
+(all cores and one thread).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--config 1..5] [--precision fp16x3|bf16x3|fp32_direct|fp64_direct]
-                  [--solve-iters I] [--no-solve]
+                  [--solve-iters I] [--no-solve] [--large-steps L]
 
---impl reference times the FP64 CPU oracle on this machine's host cores on a
-bounded sample of the same workload (the paper's method as plainly stated).
+--impl reference times the FP64 CPU oracle on this machine's host cores:
+every step is one evaluation on the same bounded visibility sample at full
+image size, whose rate is the whole workload's (the cost is exactly Z N^2;
+the line says so with "extrapolated": true).
 Multi-GPU: replicas only (each rank evaluates its own copy of the workload).
 """
 from __future__ import annotations
@@ -148,23 +153,48 @@ def make_data(config: int, shared_image: bool = False):
     return ds
 
 
-def cpu_baseline(ds, budget_s: float = 12.0):
-    """FP64 oracle (as it stands) on a visibility subsample at full image size."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_sample(ds, z: int):
+    """The data set restricted to z evenly spaced visibilities of its first
+    channel, at full image size (the oracle's cost is exactly Z N^2)."""
     import oracle
     P = oracle.Problem.from_dataset(ds)
-    N = ds.N
-    img = np.maximum(ds.truth.astype(np.float64), ds.G)
-    z = 64
+    idx = np.linspace(0, int(ds.offsets[1]) - 1, z).astype(np.int64)
+    return oracle.Problem(ds.N, ds.dx, ds.dy, P.u[idx], P.v[idx], P.vo[idx], P.sigma[idx], P.pb[:1],
+                          np.array([0, z]), P.G, P.lam)
+
+
+def _size_sample(ds, img, target_s: float) -> int:
+    """Largest visibility count (doubling from 64) whose oracle evaluation
+    takes about target_s with the current thread count."""
+    import oracle
+    z, zmax = 64, int(ds.offsets[1])
     while True:
-        idx = np.linspace(0, ds.Z - 1, z).astype(np.int64)
-        sub = oracle.Problem(N, ds.dx, ds.dy, P.u[idx], P.v[idx], P.vo[idx], P.sigma[idx], P.pb[:1],
-                             np.array([0, z]), P.G, P.lam)
+        sub = _oracle_sample(ds, z)
         t0 = time.perf_counter()
         oracle.objective_grad(sub, img[:1])
         dt = time.perf_counter() - t0
-        if dt > budget_s / 4 or z >= ds.Z:
-            break
-        z = min(ds.Z, int(z * max(2.0, min(8.0, budget_s / 4 / max(dt, 1e-3)))))
+        if dt > target_s / 2 or z >= zmax:
+            return z
+        z = min(zmax, int(z * max(2.0, min(8.0, target_s / max(dt, 1e-3)))))
+
+
+def _time_oracle(ds, img, budget_s: float):
+    import oracle
+    z = _size_sample(ds, img, budget_s / 4)
+    sub = _oracle_sample(ds, z)
     evals = 0
     t0 = time.perf_counter()
     while True:
@@ -173,39 +203,146 @@ def cpu_baseline(ds, budget_s: float = 12.0):
         if time.perf_counter() - t0 >= budget_s / 2:
             break
     dt = time.perf_counter() - t0
-    value = z * N * N * evals / dt
-    return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    return z * ds.N * ds.N * evals / dt, z, evals, dt
+
+
+def cpu_baseline(ds, budget_s: float = 12.0, single_budget_s: float = 6.0):
+    """FP64 oracle (as it stands) on a visibility subsample at full image
+    size: all host cores (OpenMP) and one thread."""
+    import oracle
+    img = np.maximum(ds.truth.astype(np.float64), ds.G)
+    cores = oracle.num_threads()
+    value, z, evals, dt = _time_oracle(ds, img, budget_s)
+    single = None
+    if single_budget_s > 0:
+        oracle.set_num_threads(1)
+        try:
+            v1, z1, e1, d1 = _time_oracle(ds, img, single_budget_s)
+        finally:
+            oracle.set_num_threads(cores)
+        single = {"value": v1, "unit": UNIT, "cores": 1,
+                  "sample": f"{e1} evaluation(s) on {z1} of {ds.Z} visibilities in {d1:.1f} s"}
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{evals} objective+gradient evaluation(s) on {z} of {ds.Z} visibilities "
-                      f"(evenly spaced) at full {N}x{N}, FP64 factored order, OpenMP"}
+                      f"(evenly spaced) at full {ds.N}x{ds.N} in {dt:.1f} s, FP64 factored order, OpenMP; "
+                      f"the rate extrapolates to the whole workload exactly (cost is Z N^2)",
+            "single_thread": single, "cpu_model": cpu_model(), "os_cpu_count": os.cpu_count()}
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: every step is one FP64 objective +
+    gradient evaluation on the same bounded visibility sample (full image
+    size), timed on the host's cores.  value = the sampled vis*pixel / the
+    step's wall time, which is the whole workload's rate (the cost is exactly
+    Z N^2); ms_per_step is the sampled step's wall time as run."""
     if rank != 0:
         return 0
+    t_start = time.perf_counter()
     ds = make_data(args.config, args.shared_image)
     import oracle
     oracle.build()
-    per = []
-    info = None
+    img = np.maximum(ds.truth.astype(np.float64), ds.G)
+    per_step_s = min(3.0, 60.0 / max(1, args.warmup + args.steps))
+    z = _size_sample(ds, img, per_step_s)
+    sub = _oracle_sample(ds, z)
+    ms = []
     for k in range(args.warmup + args.steps):
-        b = cpu_baseline(ds, budget_s=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
+        t0 = time.perf_counter()
+        oracle.objective_grad(sub, img[:1])
+        dt = (time.perf_counter() - t0) * 1e3
         if k >= args.warmup:
-            per.append(b["value"])
-            info = b
-    value = statistics.mean(per)
-    # one step of the full workload at the sampled rate (each timed step is a
-    # bounded sample of it; see cpu_baseline.sample)
-    ms_full = ds.Z * ds.N * ds.N / value * 1e3 if value > 0 else None
+            ms.append(dt)
+    ms_step = statistics.mean(ms)
+    sampled_units = z * ds.N * ds.N
+    value = sampled_units / (ms_step * 1e-3)
+    wall = time.perf_counter() - t_start
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_full, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.config] + (
                 ", one image shared by all channels (Eq. chi2-multi)" if args.shared_image else ""),
                 "precision": "fp64 oracle (CPU)"},
-            "cpu_baseline": dict(info, value=value),
+            "extrapolated": True,
+            "sample": {"visibilities": z, "of": ds.Z, "image": f"{ds.N}x{ds.N}",
+                       "vis_pixel_per_step": sampled_units,
+                       "full_workload_ms_per_step": ds.Z * ds.N * ds.N / value * 1e3,
+                       "wall_s": wall},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"each step: one objective+gradient evaluation on {z} of {ds.Z} "
+                                       f"visibilities (evenly spaced) at full {ds.N}x{ds.N}, FP64, OpenMP",
+                             "cpu_model": cpu_model(), "os_cpu_count": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def roofline(kprof: dict, units: int, config: int) -> dict:
+    """Roofline object of the dominant kernel from per-launch CUDA-event times.
+    Each launch is timed alone (events around it), so the split forms are held
+    against the burst bf16 peak; the fp16 dense rate is the same."""
+    peaks, src = _peaks()
+    dom = max(kprof.items(), key=lambda kv: kv[1][0]) if kprof else ("none", (0.0, 1))
+    name, (tot_ms, cnt) = dom
+    avg_ms = tot_ms / max(cnt, 1)
+    # algorithmic work: 4 flops per (visibility, pixel) pair for each operator pass
+    flops = 4.0 * units
+    if name.startswith(("fwd", "adj")) and not name.endswith("reduce"):
+        achieved = flops / (avg_ms * 1e-3) / 1e12
+        if name in ("fwd_tc", "fwd_rs", "adj_tc"):
+            peak = peaks.get("bf16_tflops")
+            sus = peaks.get("bf16_tflops_sustained", peak)
+            return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": _traffic(name) if config == 2 else None,
+                    "executed_frac": 3 * achieved / peak, "algorithmic_cap": 1.0 / 3.0,
+                    "note": f"{name}{' (+ slice combination)' if name == 'fwd_rs' else ''}: "
+                            f"{avg_ms:.3f} ms/launch, 4 algorithmic flops per vis*pixel "
+                            f"(12 executed in the 3-term split, so the algorithmic fraction is capped at 1/3: "
+                            f"executed {3 * achieved:.0f} TFLOP/s); peak = {src} burst bf16 "
+                            f"(of sustained: {achieved / sus:.3f})"}
+        return {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "note": f"{name}: {avg_ms:.3f} ms/launch"}
+    return {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+            "frac": None, "traffic": None, "note": name}
+
+
+def large_block(precision: str, steps: int, warmup: int = 3, config: int = 5) -> dict:
+    """Device-timed evaluations of the largest single-image workload (1024^2,
+    2.0e7 visibilities), with its own per-kernel roofline; L2 flushed between
+    steps (its inputs are also larger than L2)."""
+    import torch
+    from paper_1703_02920_gb300 import memsynth
+    ds = make_data(config)
+    units = ds.Z * ds.N * ds.N
+    ctx = memsynth.Context(ds, precision=precision)
+    img = torch.from_numpy(np.maximum(ds.truth, ds.G)).cuda()
+    grad = torch.empty_like(img)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tiles = list(ctx.autotune(img, reps=1)) if precision in ("bf16x3", "fp16x3") else None
+    for _ in range(warmup):
+        memsynth.mem_objective_grad(ctx.handle, img, grad, 0, want_scalars=False)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    l0 = ctx.launches()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(ctx.stream)
+        memsynth.mem_objective_grad(ctx.handle, img, grad, 0, want_scalars=False)
+        ev[k][1].record(ctx.stream)
+    torch.cuda.synchronize()
+    launches = ctx.launches() - l0
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    ctx.profile(True)
+    ctx.profile_read()
+    for _ in range(2):
+        flush.zero_()
+        memsynth.mem_objective_grad(ctx.handle, img, grad, 0, want_scalars=False)
+    kprof = ctx.profile_read()
+    ctx.profile(False)
+    ctx.close()
+    return {"workload": WORKLOADS[config], "precision": precision, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT, "gpu_launches": launches,
+            "tiles": tiles, "roofline": roofline(kprof, units, config),
+            "kernels": {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1]} for k, v in kprof.items()}}
 
 
 def run_sweep(args):
@@ -263,6 +400,9 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="only W + K objective+gradient evaluations with the default tiling (for ncu captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--large-steps", type=int, default=10,
+                    help="device-timed steps of the 1024^2, 2e7-visibility workload reported beside the "
+                         "main line (0: skip)")
     ap.add_argument("--shared-image", action="store_true",
                     help="one image for all channels (multi-frequency mode); meaningful for the cube config 4")
     ap.add_argument("--sweep", action="store_true",
@@ -371,28 +511,7 @@ def main():
     e2e_val = job_value(units, world, max_over_ranks(statistics.mean(e2e_ms), dist, "cuda"))
 
     # ---- roofline of the dominant kernel (algorithmic flops per launch / event time)
-    peaks, src = _peaks()
-    dom = max(kprof.items(), key=lambda kv: kv[1][0]) if kprof else ("none", (0.0, 1))
-    name, (tot_ms, cnt) = dom
-    avg_ms = tot_ms / max(cnt, 1)
-    # algorithmic work: 4 flops per (visibility, pixel) pair for each operator pass
-    flops = 4.0 * units
-    if name.startswith(("fwd", "adj")) and not name.endswith("reduce"):
-        achieved = flops / (avg_ms * 1e-3) / 1e12
-        if name in ("fwd_tc", "fwd_rs", "adj_tc"):  # both split forms run kind::f16 MMAs at the bf16 rate
-            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": _traffic(name) if args.config == 2 else None,
-                    "note": f"{name}{' (+ slice combination)' if name == 'fwd_rs' else ''}: "
-                            f"{avg_ms:.3f} ms/launch, 4 algorithmic flops per vis*pixel "
-                            f"(12 executed in the 3-term split: executed {3 * achieved:.0f} TFLOP/s); "
-                            f"peak = {src} sustained bf16 (fp16 dense rate is the same)"}
-        else:
-            roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
-                    "frac": None, "traffic": None, "note": f"{name}: {avg_ms:.3f} ms/launch"}
-    else:
-        roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                "frac": None, "traffic": None, "note": name}
+    roof = roofline(kprof, units, args.config)
     kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1],
                    "share": v[0] / max(sum(x[0] for x in kprof.values()), 1e-30)} for k, v in kprof.items()}
 
@@ -449,6 +568,10 @@ def main():
         else:
             solve["fp64"] = "not run: over a minute per iteration at this size"
 
+    large = None
+    if args.large_steps > 0 and args.config != 5 and not args.shared_image:
+        large = large_block(args.precision, args.large_steps)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ds)
@@ -470,7 +593,8 @@ def main():
                         "d2h_bytes_per_step": int(img.numel() * 4 + 24)},
                 "gpu_launches": launches,
                 "roofline": roof, "kernels": kernels,
-                "clocks": clk.summary(), "cpu_baseline": cpu, "solve": solve, "gridded_forward": gridded}
+                "clocks": clk.summary(), "cpu_baseline": cpu, "solve": solve, "gridded_forward": gridded,
+                "largest_single_image": large}
         print(json.dumps(line))
     ctx.close()
     return 0

@@ -40,7 +40,10 @@
  * Errors.  Every call returns a mem_status; nothing is thrown across the ABI.
  * mem_last_error() gives a message for the last failing call of a context.
  * Device-side waits are bounded (mem_config.spin_limit); a wait that runs out
- * makes the call return MEM_ETIMEOUT without faulting the GPU.  A non-finite
+ * makes the call return MEM_ETIMEOUT without faulting the GPU.  The last wait
+ * of a tensor-core kernel, for its own operations and copies already in
+ * flight (they must finish before their memory is released), is bounded by
+ * max(spin_limit, 2^24) polls.  A non-finite
  * objective returns MEM_ENUMERIC.  There is no CPU fallback: without a usable
  * sm_103a GPU, mem_create returns MEM_ECUDA.
  */
@@ -319,9 +322,13 @@ int32_t mem_profile_read(mem_ctx *ctx, int32_t max_kernels, char *names, double 
  * GPU race and must be serialised by the caller.  The array keeps the last
  * call's contents; nothing in it needs clearing between calls.  The first
  * call on a device resolves the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.
- * The call is synchronous on `stream` (it reads back a device status word)
- * and returns MEM_ETIMEOUT if a bounded device-side wait ran out. */
+ * with that device current) and keeps it for the life of the process, so the
+ * call must not be used after cudaDeviceReset.  `stream` must belong to the
+ * device current at the call.  Every call uploads its work list from host
+ * memory and reads a device status word back, synchronising `stream`: never
+ * make it while `stream` (or, in global capture mode, any stream of the
+ * process) is being captured.  Returns MEM_ETIMEOUT if a bounded device-side
+ * wait ran out. */
 mem_status mem_adjoint_noalloc(int32_t n, double dx, double dy, int64_t n_vis,
                                const double *u_dev, const double *v_dev, const float *y_dev,
                                const float *pb_dev, float *img_dev, void *stream);

@@ -199,3 +199,15 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads used by the following calls (n >= 1); for timing the oracle on one
+ * core beside all of them.  The sums do not depend on it: every output is
+ * summed by one thread in index order. */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -67,12 +67,19 @@ def _lib():
             lib.orc_adjoint_factored_full.argtypes = [I, D, D, I64, P, P, P, P]
             lib.orc_adjoint_factored_full.restype = None
             lib.orc_num_threads.restype = ctypes.c_int
+            lib.orc_set_num_threads.argtypes = [I]
+            lib.orc_set_num_threads.restype = None
             _LIB = lib
         return _LIB
 
 
 def num_threads() -> int:
     return int(_lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads for the following operator sums (results do not depend on it)."""
+    _lib().orc_set_num_threads(int(n))
 
 
 def _p(a: np.ndarray):

@@ -148,6 +148,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
     return true;
 }
 
+// Bound for the end-of-kernel waits on the CTA's own in-flight tensor-core
+// operations and bulk copies.  Those were issued with complete operands and
+// finish within microseconds, but they must finish before TMEM or shared
+// memory is released, so the bound is the context's spin limit and never fewer
+// than 2^24 polls (a spin limit small enough to force a timeout elsewhere must
+// not cut these waits short).
+__device__ __forceinline__ uint64_t drain_limit(uint64_t spin) {
+    return spin > (1ull << 24) ? spin : (1ull << 24);
+}
+
 // 1-D bulk async copy global -> shared, completion counted on an mbarrier.
 // Both addresses 16-byte aligned, size a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {

@@ -151,7 +151,8 @@ void launch_adj_tc(const DevData& d, int f16, const AdjUnit* units, const int* c
 // increments: the caller passes d.u, d.v, d.dx, d.dy; d.pa / d.pb are unused.
 void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_unit_off, int n_ctas,
                       const float2* y, float* partial, uint64_t spin, int* status, cudaStream_t st);
-// out[p] = A[p] * sum of unit partials (single channel, unit order, FP64 sum).
+// out[p] = A[p] * sum of unit partials (single channel, unit order,
+// compensated FP32 two-sum).
 void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partial, const float* beam,
                               float* out, cudaStream_t st);
 // Sum unit partials per channel (unit order) into gsum[C][N*N].

@@ -21,6 +21,14 @@
 // accumulators (2 x BN columns) let the epilogue of one tile overlap the MMAs
 // of the next.
 //
+// Each accumulation covers at most F2_KSEG image rows (a K segment): the
+// tensor core adds every MMA's product sum to its FP32 accumulator rounding
+// towards zero, a shrink of up to one ulp per MMA that grows with the number
+// of MMAs per accumulation.  Larger images run several segments per column
+// block, each into a fresh accumulator; the epilogue folds every segment into
+// the same compensated per-visibility sums (V is linear in T), so the shrink
+// stays at the level of a 256-row image whatever N is.
+//
 // Roles (448 threads): warps 0-3 epilogue (TMEM lane = A row), warp 4 MMA
 // issuer + TMEM owner, warp 5 bulk copies of the image operand chunks,
 // warps 6-13 Ey producers.  Every mbarrier wait is bounded.
@@ -37,6 +45,7 @@ constexpr int F2_MAX_STAGES = 4;
 constexpr int F2_THREADS = 448;
 constexpr int F2_APLANE = 128 * TC_BK * 2;  // bytes of one A plane (hi or lo), 8 KB
 constexpr int F2_ABYTES = 2 * F2_APLANE;
+constexpr int F2_KSEG = 256;                 // image rows per accumulation (at most)
 
 __host__ __device__ inline int f2_stage_bytes(int BN) { return F2_ABYTES + 2 * BN * TC_BK * 2; }
 __host__ __device__ inline uint32_t f2_tmem_cols(int BN) {
@@ -71,6 +80,9 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
     const int N = d.N, c0 = N / 2;
     const int BN = d.fwd_bn;
     const int n_mb = N / BN, nk = N / TC_BK;
+    // stages per accumulation and accumulations per column block
+    const int kseg = nk < F2_KSEG / TC_BK ? nk : F2_KSEG / TC_BK;
+    const int n_seg = nk / kseg;
     const int stage_bytes = f2_stage_bytes(BN);
     const uint32_t tcols = f2_tmem_cols(BN);
     const int64_t NN = (int64_t)N * N;
@@ -109,13 +121,14 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             uint32_t sc = 0, it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                for (int mb = 0; mb < n_mb && ok; ++mb, ++it) {
+                for (int u = 0; u < n_mb * n_seg && ok; ++u, ++it) {
                     const int b = it & 1;
+                    const int ks0 = (u % n_seg) * kseg;  // first stage of this accumulation
                     ok = mbar_wait(&S.tempty[b], ((it >> 1) & 1) ^ 1, spin, abort, status);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t dt = tmem + (uint32_t)(b * BN);
-                    for (int ks = 0; ks < nk; ++ks, ++sc) {
+                    for (int ks = ks0; ks < ks0 + kseg; ++ks, ++sc) {
                         const int s = sc % F2_STAGES;
                         ok = mbar_wait(&S.full[s], (sc / F2_STAGES) & 1, spin, abort, status) &&
                              mbar_wait(&S.bfull[s], (sc / F2_STAGES) & 1, spin, abort, status);
@@ -130,7 +143,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                             const uint64_t a_l = smem_desc(A + F2_APLANE + ao, 2048, 128);
                             const uint64_t b_h = smem_desc(B + bo, lboB, 128);
                             const uint64_t b_l = smem_desc(B + BN * TC_BK * 2 + bo, lboB, 128);
-                            const uint32_t acc = (ks > 0 || kk > 0) ? 1u : 0u;
+                            const uint32_t acc = (ks > ks0 || kk > 0) ? 1u : 0u;
                             umma_bf16(dt, a_h, b_h, idesc, acc);
                             umma_bf16(dt, a_h, b_l, idesc, 1u);
                             umma_bf16(dt, a_l, b_h, idesc, 1u);
@@ -144,7 +157,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             // were complete when it was issued)
             umma_commit(&S.drain);
             int dummy = 0;
-            mbar_wait(&S.drain, 0, 1ull << 32, (volatile int*)&dummy, status);
+            mbar_wait(&S.drain, 0, drain_limit(spin), (volatile int*)&dummy, status);
         }
         __syncwarp();
     } else if (warp == 5) {
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                 // the CTA's shared memory is released
                 int dummy = 0;
                 for (uint32_t q = (sc > F2_STAGES ? sc - F2_STAGES : 0); q < sc; ++q)
-                    mbar_wait(&S.bfull[q % F2_STAGES], (q / F2_STAGES) & 1, 1ull << 32,
+                    mbar_wait(&S.bfull[q % F2_STAGES], (q / F2_STAGES) & 1, drain_limit(spin),
                               (volatile int*)&dummy, status);
             }
         }
@@ -280,8 +293,12 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             const float osc = F16 ? cscale[tl.chan] : 1.f;  // operand scale (power of two)
             scomp *= osc;
             float s0 = 0.f, s1 = 0.f, c0s = 0.f, c1s = 0.f;  // compensated sums
-            for (int mb = 0; mb < n_mb; ++mb, ++it) {
+            for (int u = 0; u < n_mb * n_seg; ++u, ++it) {
+                const int mb = u / n_seg;
                 const int b = it & 1;
+                // the column-mean term c_m S_k enters once per column: with the
+                // block's first segment only
+                const float sterm = (u % n_seg == 0) ? scomp : 0.f;
                 ok = __all_sync(0xffffffffu,
                                 mbar_wait(&S.tfull[b], (it >> 1) & 1, spin, abort, status, 256));
                 if (!ok) break;
@@ -301,7 +318,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) *(float4*)(cq + 2 * k) = ((const float4*)(cmw + m0))[k];
                     // packed pairs (even k, odd k), added at the end
-                    const float2 ss = make_float2(scomp, scomp);
+                    const float2 ss = make_float2(sterm, sterm);
                     float2 ux = {0.f, 0.f}, uy = {0.f, 0.f}, wx = {0.f, 0.f}, wy = {0.f, 0.f};
 #pragma unroll
                     for (int p = 0; p < 4; ++p) {

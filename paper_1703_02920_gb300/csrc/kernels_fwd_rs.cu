@@ -174,8 +174,8 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             // resident-operand copy lands before shared memory is released
             umma_commit(&S.drain);
             int dummy = 0;
-            mbar_wait(&S.drain, 0, 1ull << 32, (volatile int*)&dummy, status);
-            if (!ok && nres > 0) mbar_wait(&S.bres, (nres - 1) & 1, 1ull << 32, (volatile int*)&dummy, status);
+            mbar_wait(&S.drain, 0, drain_limit(spin), (volatile int*)&dummy, status);
+            if (!ok && nres > 0) mbar_wait(&S.bres, (nres - 1) & 1, drain_limit(spin), (volatile int*)&dummy, status);
         }
         __syncwarp();
     } else if (warp >= 5) {

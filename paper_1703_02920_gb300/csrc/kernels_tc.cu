@@ -31,7 +31,8 @@ namespace msk {
 // Adjoint: split-K over visibilities.  A CTA owns a contiguous run of
 // (channel, output block, visibility range) units, accumulates each unit's
 // BLK x BLK block of G in TMEM over 16-visibility stages and drains it to an
-// FP32 partial buffer; partials are summed in unit order in FP64 afterwards.
+// FP32 partial buffer; partials are summed in unit order afterwards (compensated
+// FP32 two-sum).
 // Operands are MN-major (8 consecutive pixels of one visibility per 16-byte
 // core-matrix row), the layout the per-visibility phase recurrences produce.
 // Roles: warp 4 MMA + TMEM owner; the other 13 warps produce operand stages,
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             }
             umma_commit(&S.drain);
             int dummy = 0;
-            mbar_wait(&S.drain, 0, 1ull << 32, (volatile int*)&dummy, status);
+            mbar_wait(&S.drain, 0, drain_limit(spin), (volatile int*)&dummy, status);
         }
         __syncwarp();
     } else {
@@ -389,7 +390,8 @@ void launch_adj_tc_uv(const DevData& d, const AdjUnit* units, const int* cta_uni
                                                     status, st);
 }
 
-// Single channel: out[p] = A[p] * (unit partials summed in unit order, FP64).
+// Single channel: out[p] = A[p] * (unit partials summed in unit order,
+// compensated FP32 (two-sum)).
 __global__ void __launch_bounds__(256) k_adj_tc_reduce_out(int N, const int* __restrict__ cb_unit_off,
                                                            const float* __restrict__ partial,
                                                            const float* __restrict__ beam,
@@ -416,8 +418,8 @@ void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partia
     k_adj_tc_reduce_out<<<prep_blocks(N), 256, 0, st>>>(N, cb_unit_off, partial, beam, out);
 }
 
-// Sum the unit partials of each (channel, block) in unit order (FP64) into
-// gsum[c][N*N] (without the beam factor).
+// Sum the unit partials of each (channel, block) in unit order (compensated
+// FP32, stored as FP64) into gsum[c][N*N] (without the beam factor).
 __global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __restrict__ cb_unit_off,
                                                        const float* __restrict__ partial,
                                                        const float* __restrict__ ymax,

@@ -15,7 +15,13 @@
 // overlap on the GPU (different streams, threads or processes sharing a
 // context) race; serialise them.  The array keeps the previous call's
 // contents; nothing in it needs to start at zero (each partial block is fully
-// written before it is read).
+// written before it is read, and the reduction reads only the partials of the
+// units this call listed).  The status word is cleared on every call.
+//
+// The arrays' device addresses are resolved once per device and kept for the
+// life of the process; after cudaDeviceReset the library's device image is
+// loaded again at new addresses, so the entry point must not be used after a
+// device reset in the same process.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -93,6 +99,9 @@ extern "C" mem_status mem_adjoint_noalloc(int32_t n, double dx, double dy, int64
         return MEM_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    // clear an error the caller may have left pending, so that a failure
+    // reported below is this call's own
+    cudaGetLastError();
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
