@@ -12,9 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmemsynth.so")
-SOURCES = ["api.cu", "kernels_simt.cu", "kernels_tc.cu", "kernels_fwd.cu", "kernels_fwd_rs.cu", "noalloc.cu",
+SOURCES = ["api.cu", "kernels_simt.cu", "kernels_tc.cu", "kernels_fwd.cu", "kernels_fwd_rs.cu", "noalloc.cu", "solver.cu",
            "gridded.cu"]
-HEADERS = ["common.cuh", "internal.h"]
+HEADERS = ["common.cuh", "internal.h", "solver.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -17,219 +17,13 @@
 
 #include "../../include/libmemsynth.h"
 #include "internal.h"
+#include "solver.h"
 
 using namespace msk;
 
 namespace {
 
 thread_local std::string g_last_error = "";
-
-// Projected Polak-Ribiere CG and line-search constants.  The paper names a
-// Numerical-Recipes style CG with bracketing and Brent line minimisation
-// (Section 4.2) without giving constants; these are this library's reading.
-constexpr double GOLD = 1.618033988749895;    // bracket expansion ratio
-constexpr double CGOLD = 0.3819660112501051;  // golden-section fraction
-constexpr double SHRINK = 0.25;               // trial-step reduction
-constexpr int LS_MAX_EVALS = 20;              // objective evaluations per line search
-constexpr double LS_TOL = 1e-3;               // relative step tolerance (Brent)
-constexpr double LS_EPS = 1e-10;              // absolute tolerance / first trial step
-constexpr int RESTART = 50;                   // steepest-descent restart period
-constexpr double POLISH = 0.2;                // half-width of the final 3-point Newton step / step
-
-// Line search on phi(alpha), alpha >= 0, as a resumable state machine so that
-// many images (cube channels) can share each batched objective evaluation.
-// Bracketing: shrink the trial step until phi < phi(0), or expand it by GOLD
-// while phi keeps falling; then Brent's method (Brent 1973, ch. 5); then one
-// Newton step on central differences over x -/+ h, h = min(POLISH alpha0,
-// x / 2), clamped to that interval.  Brent stops anywhere inside its tolerance; the last step moves
-// the result to within O(tol^2) of the minimiser by a formula continuous in
-// the objective values, so different roundings give the same step.
-struct LineSearch {
-    enum Phase { INIT, SHRINK_P, EXPAND, BRENT, POL_P, POL_M, DONE } phase = DONE;
-    double px = 0, pfx = 0, ph = 0, pfp = 0;
-    int evals = 0, nb = 0, budget = 0;
-    double f0 = 0, a = 0, fa = 0, b = 0, fb = 0, c = 0, fc = 0, eps = 0, a0 = 0;
-    double lo = 0, hi = 0, x = 0, w = 0, v = 0, fx = 0, fw = 0, fv = 0, d = 0, e = 0;
-    double req = 0, alpha = 0, falpha = 0;
-
-    void start(double phi0, double alpha0) {
-        a0 = alpha0;
-        f0 = phi0;
-        eps = LS_EPS * alpha0;
-        a = 0.0;
-        fa = phi0;
-        b = alpha0;
-        req = b;
-        evals = 0;
-        phase = INIT;
-    }
-    bool running() const { return phase != DONE; }
-    void finish(double al, double f) {
-        if (al > 0.0) {
-            px = al;
-            pfx = f;
-            ph = std::min(POLISH * a0, 0.5 * al);
-            req = px + ph;
-            phase = POL_P;
-            return;
-        }
-        alpha = al;
-        falpha = f;
-        phase = DONE;
-    }
-    void shrink_check() {
-        if (fb >= fa && evals < LS_MAX_EVALS) {
-            c = b;
-            fc = fb;
-            b = b * SHRINK;
-            req = b;
-            phase = SHRINK_P;
-        } else if (fb >= fa) {
-            finish(0.0, f0);
-        } else {
-            brent_start();
-        }
-    }
-    void expand_check() {
-        if (fc < fb && evals < LS_MAX_EVALS) {
-            a = b;
-            fa = fb;
-            b = c;
-            fb = fc;
-            c = b + GOLD * (b - a);
-            req = c;
-            phase = EXPAND;
-        } else if (fc < fb) {
-            finish(c, fc);
-        } else {
-            brent_start();
-        }
-    }
-    void brent_start() {
-        lo = a;
-        hi = c;
-        x = w = v = b;
-        fx = fw = fv = fb;
-        d = e = 0.0;
-        nb = 0;
-        budget = LS_MAX_EVALS - evals;
-        phase = BRENT;
-        brent_step();
-    }
-    void brent_step() {
-        if (nb >= budget) {
-            evals += nb;
-            finish(x, fx);
-            return;
-        }
-        const double xm = 0.5 * (lo + hi);
-        const double tol1 = LS_TOL * std::fabs(x) + eps;
-        const double tol2 = 2.0 * tol1;
-        if (std::fabs(x - xm) <= tol2 - 0.5 * (hi - lo)) {
-            evals += nb;
-            finish(x, fx);
-            return;
-        }
-        bool golden = true;
-        if (std::fabs(e) > tol1) {
-            double r = (x - w) * (fx - fv);
-            double q = (x - v) * (fx - fw);
-            double p = (x - v) * q - (x - w) * r;
-            q = 2.0 * (q - r);
-            if (q > 0.0) p = -p;
-            else q = -q;
-            const double e_prev = e;
-            e = d;
-            if (std::fabs(p) < std::fabs(0.5 * q * e_prev) && p > q * (lo - x) && p < q * (hi - x)) {
-                d = p / q;
-                const double t = x + d;
-                if ((t - lo) < tol2 || (hi - t) < tol2) d = (xm >= x) ? tol1 : -tol1;
-                golden = false;
-            }
-        }
-        if (golden) {
-            e = (x >= xm) ? (lo - x) : (hi - x);
-            d = CGOLD * e;
-        }
-        req = (std::fabs(d) >= tol1) ? x + d : x + (d >= 0.0 ? tol1 : -tol1);
-    }
-    void feed(double f) {
-        switch (phase) {
-            case INIT:
-                fb = f;
-                evals = 1;
-                if (fb >= fa) {
-                    c = b;
-                    fc = fb;
-                    shrink_check();
-                } else {
-                    c = b + GOLD * (b - a);
-                    req = c;
-                    phase = EXPAND;
-                }
-                break;
-            case SHRINK_P:
-                fb = f;
-                evals += 1;
-                shrink_check();
-                break;
-            case EXPAND:
-                fc = f;
-                evals += 1;
-                expand_check();
-                break;
-            case BRENT: {
-                const double t = req, ft = f;
-                nb += 1;
-                if (ft <= fx) {
-                    if (t >= x) lo = x;
-                    else hi = x;
-                    v = w;
-                    fv = fw;
-                    w = x;
-                    fw = fx;
-                    x = t;
-                    fx = ft;
-                } else {
-                    if (t < x) lo = t;
-                    else hi = t;
-                    if (ft <= fw || w == x) {
-                        v = w;
-                        fv = fw;
-                        w = t;
-                        fw = ft;
-                    } else if (ft <= fv || v == x || v == w) {
-                        v = t;
-                        fv = ft;
-                    }
-                }
-                brent_step();
-                break;
-            }
-            case POL_P:
-                pfp = f;
-                evals += 1;
-                req = px - ph;
-                phase = POL_M;
-                break;
-            case POL_M: {
-                const double fm = f;
-                evals += 1;
-                double x = px;
-                const double curv = pfp - 2.0 * pfx + fm;
-                if (curv > 0.0) {
-                    const double t = px - ph * (pfp - fm) / (2.0 * curv);
-                    x = std::min(std::max(t, px - ph), px + ph);
-                }
-                alpha = x;
-                phase = DONE;
-                break;
-            }
-            case DONE:
-                break;
-        }
-    }
-};
 
 size_t alloc_cap() {
     const char* s = std::getenv("MEMSYNTH_MAX_BYTES");
@@ -303,7 +97,15 @@ struct mem_ctx {
     };
     bool graphs = true;
     cudaStream_t cap_st = nullptr;
-    GraphSlot g_objgrad, g_solve_objgrad, g_solve_curv, g_solve_probe;
+    GraphSlot g_objgrad;
+    // the whole solve (evaluations, CG and line-search control) as one graph
+    // with conditional WHILE nodes for the iterations and the probes
+    struct SolveGraph {
+        cudaGraphExec_t exec = nullptr;
+        int prec = -1;
+        const void* hist = nullptr;
+        int64_t n_pro = 0, n_iter = 0, n_probe = 0;  // kernel launches per part
+    } g_solve;
 
     // tensor-core tiling (autotuned): forward kernel (MEM_FWD_STREAM: image
     // operand streamed per tile, column block fwd_bn; MEM_FWD_RESIDENT: image
@@ -336,6 +138,10 @@ struct mem_ctx {
     double *I64 = nullptr, *d64 = nullptr, *g64 = nullptr, *gf64 = nullptr, *gp64 = nullptr;
     double *alpha = nullptr, *beta = nullptr, *dots = nullptr, *dpart = nullptr;
     int* mode = nullptr;
+    CgImage* cg_st = nullptr;
+    CgControl* cg_ctl = nullptr;
+    double* cg_hist = nullptr;
+    size_t cg_hist_cap = 0;
 
     DevData dd() const {
         DevData d;
@@ -718,9 +524,8 @@ void drop_graph(mem_ctx::GraphSlot& g) {
 
 void drop_graphs(mem_ctx* c) {
     drop_graph(c->g_objgrad);
-    drop_graph(c->g_solve_objgrad);
-    drop_graph(c->g_solve_curv);
-    drop_graph(c->g_solve_probe);
+    if (c->g_solve.exec) cudaGraphExecDestroy(c->g_solve.exec);
+    c->g_solve = mem_ctx::SolveGraph();
 }
 
 // Run `body` (kernel launches on c->st only) through the graph slot: replay
@@ -890,6 +695,160 @@ void tune_store(const mem_ctx* c) {
 
 }  // namespace
 
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// The solve's launch sequences (projected PR-CG, Eq. minproblem), shared by
+// the graph and by the host-driven path (graphs off, or per-kernel timing).
+// Non-zero handles are the conditional nodes the controller kernels steer.
+// ---------------------------------------------------------------------------
+mem_status solve_prologue(mem_ctx* c, unsigned long long h_outer) {
+    ImgSrc src{nullptr, c->I64, nullptr, nullptr, c->G, 0};
+    TRY(run_objgrad(c, src, 1, nullptr, c->gf64, c->g64));
+    launch_cg_init(c->n_images, c->cg_st, c->cg_ctl, c->scal, c->cg_hist, c->dstatus, h_outer, c->st);
+    c->launches++;
+    return after_launch(c, "solver start");
+}
+
+// beta, direction (and its restart), slope, curvature, first trial step
+mem_status solve_iter_head(mem_ctx* c, unsigned long long h_inner) {
+    const DevData d = c->dd();
+    const int NI = c->n_images;
+    cudaStream_t st = c->st;
+    launch_dots(d, DOT_BETA, c->g64, c->gp64, nullptr, c->dpart, c->dots, st);
+    launch_cg_beta(NI, c->cg_st, c->cg_ctl, c->dots, c->beta, c->mode, st);
+    launch_cg_direction(d, c->I64, c->g64, c->beta, c->mode, c->d64, st);
+    launch_dots(d, DOT_SLOPE, c->gf64, c->d64, c->g64, c->dpart, c->dots, st);
+    launch_cg_slope(NI, c->cg_st, c->dots, c->beta, c->mode, st);
+    launch_cg_direction(d, c->I64, c->g64, c->beta, c->mode, c->d64, st);
+    launch_dots(d, DOT_SLOPE, c->gf64, c->d64, c->g64, c->dpart, c->dots, st);
+    launch_cg_slope2(NI, c->cg_st, c->cg_ctl, c->dots, c->mode, st);
+    c->launches += 11;
+    TRY(after_launch(c, "search direction"));
+    // quadratic model of chi^2 along d: curvature sum w |F(A d)|^2
+    ImgSrc src{nullptr, c->d64, nullptr, nullptr, c->G, 0};
+    TRY(run_forward(c, src, FWD_CURV, false, nullptr));
+    launch_dots(d, DOT_MAX, c->I64, c->d64, nullptr, c->dpart, c->dots, st);
+    launch_ls_start(NI, c->cg_st, c->cg_ctl, c->scal, c->dots, c->alpha, c->dstatus, h_inner, st);
+    c->launches += 3;
+    return after_launch(c, "line search start");
+}
+
+// one line-search probe: phi(alpha) = Phi(I) + [Phi(max(I + alpha d, G)) -
+// Phi(I)], the change evaluated from the image difference so that its
+// rounding error scales with the step, not with Phi
+mem_status solve_probe(mem_ctx* c, unsigned long long h_inner) {
+    ImgSrc src{nullptr, c->I64, c->d64, c->alpha, c->G, 1};
+    void* ybuf = c->prec == MEM_PREC_FP64_DIRECT ? (void*)c->y64 : (void*)c->y32;
+    TRY(run_forward(c, src, FWD_DCHI, true, ybuf));
+    launch_ls_feed(c->n_images, c->cg_st, c->cg_ctl, c->scal, c->alpha, c->dstatus, h_inner, c->st);
+    c->launches++;
+    return after_launch(c, "line search");
+}
+
+// accepted step, new gradient, history row, loop condition
+mem_status solve_iter_tail(mem_ctx* c, unsigned long long h_outer) {
+    const DevData d = c->dd();
+    const int NI = c->n_images;
+    const size_t n = (size_t)NI * c->N * c->N;
+    cudaStream_t st = c->st;
+    launch_cg_finish(NI, c->cg_st, c->cg_ctl, c->alpha, st);
+    launch_cg_step(d, c->I64, c->d64, c->alpha, st);
+    c->launches += 2;
+    CK(cudaMemcpyAsync(c->gp64, c->g64, n * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy g");
+    ImgSrc src{nullptr, c->I64, nullptr, nullptr, c->G, 0};
+    TRY(run_objgrad(c, src, 1, nullptr, c->gf64, c->g64));
+    launch_cg_record(NI, c->cg_st, c->cg_ctl, c->scal, c->cg_hist, c->dstatus, h_outer, st);
+    c->launches++;
+    return after_launch(c, "iteration end");
+}
+
+// Capture `body` (launches on c->st) into the existing graph g; the number
+// of kernel launches it made goes to *nlaunch.
+mem_status capture_into(mem_ctx* c, cudaGraph_t g, const std::function<mem_status()>& body, int64_t* nlaunch) {
+    if (!c->cap_st) CK(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking), "capture stream");
+    cudaStream_t user = c->st;
+    c->st = c->cap_st;
+    const int64_t l0 = c->launches;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(c->cap_st, g, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        c->st = user;
+        return cuda_fail(c, e, "begin capture");
+    }
+    mem_status s = body();
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(c->cap_st, &out);
+    c->st = user;
+    *nlaunch = c->launches - l0;
+    c->launches = l0;
+    if (s != MEM_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    return MEM_OK;
+}
+
+// Append a conditional WHILE node after the capture's current last nodes; the
+// capture continues after it.  *body receives the loop body graph.
+mem_status add_while_here(mem_ctx* c, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &g, &deps, &edges, &nd), "capture info");
+    if (cs != cudaStreamCaptureStatusActive || !g) return fail(c, MEM_ECUDA, "solve graph: no active capture");
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, edges, nd, &p), "conditional node");
+    *body = p.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(c->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+       "capture dependencies");
+    return MEM_OK;
+}
+
+// prologue -> WHILE(iterations) { head -> WHILE(probes) { probe } -> tail }
+mem_status build_solve_graph(mem_ctx* c) {
+    if (c->g_solve.exec) cudaGraphExecDestroy(c->g_solve.exec);
+    c->g_solve = mem_ctx::SolveGraph();
+    cudaGraph_t top = nullptr;
+    CK(cudaGraphCreate(&top, 0), "graph create");
+    auto done = [&](mem_status s) {
+        cudaGraphDestroy(top);
+        return s;
+    };
+    cudaGraphConditionalHandle h_outer = 0, h_inner = 0;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h_outer, top, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return done(cuda_fail(c, e, "conditional handle"));
+    cudaGraph_t body_outer = nullptr, body_inner = nullptr;
+    mem_ctx::SolveGraph sg;
+    mem_status s = capture_into(c, top, [&]() -> mem_status {
+        TRY(solve_prologue(c, h_outer));
+        return add_while_here(c, h_outer, &body_outer);
+    }, &sg.n_pro);
+    if (s != MEM_OK) return done(s);
+    e = cudaGraphConditionalHandleCreate(&h_inner, body_outer, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return done(cuda_fail(c, e, "conditional handle"));
+    s = capture_into(c, body_outer, [&]() -> mem_status {
+        TRY(solve_iter_head(c, h_inner));
+        TRY(add_while_here(c, h_inner, &body_inner));
+        return solve_iter_tail(c, h_outer);
+    }, &sg.n_iter);
+    if (s != MEM_OK) return done(s);
+    s = capture_into(c, body_inner, [&]() { return solve_probe(c, h_inner); }, &sg.n_probe);
+    if (s != MEM_OK) return done(s);
+    e = cudaGraphInstantiate(&sg.exec, top, 0);
+    if (e != cudaSuccess) return done(cuda_fail(c, e, "solve graph instantiate"));
+    sg.prec = c->prec;
+    sg.hist = c->cg_hist;
+    c->g_solve = sg;
+    return done(MEM_OK);
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1495,187 +1454,87 @@ mem_status mem_solve(mem_ctx* c, float* image_dev_inout, int32_t n_iter, mem_sol
     TRY(dalloc(c, &c->mode, (size_t)NI));
     TRY(dalloc(c, &c->dots, (size_t)2 * NI));
     TRY(dalloc(c, &c->dpart, (size_t)2 * NI * prep_blocks(c->N)));
-    DevData d = c->dd();
-    cudaStream_t st = c->st;
-
-    std::vector<double> sc, hd(2 * NI), alpha(NI, 0.0), beta(NI, 0.0), phi(NI), chi(NI), S(NI), slope(NI);
-    std::vector<int> mode(NI, 0), active(NI, 1), iters(NI, 0), evals_tot(NI, 0);
-    std::vector<double> hist((size_t)NI * (n_iter + 1) * 6, 0.0);
-    int stopped_early = 0;
-
-    auto objgrad = [&]() -> mem_status {
-        ImgSrc src{nullptr, c->I64, nullptr, nullptr, c->G, 0};
-        TRY(graphed(c, c->g_solve_objgrad, c->I64, c->gf64, 1,
-                    [&]() { return run_objgrad(c, src, 1, nullptr, c->gf64, c->g64); }));
-        TRY(read_scalars(c, sc));
-        for (int i = 0; i < NI; ++i) {
-            phi[i] = sc[3 + 3 * i];
-            chi[i] = sc[4 + 3 * i];
-            S[i] = sc[5 + 3 * i];
-        }
-        return MEM_OK;
-    };
-    auto put_hist = [&](int i, int k, double a, double b, double ev) {
-        double* h = &hist[((size_t)i * (n_iter + 1) + k) * 6];
-        h[0] = phi[i];
-        h[1] = chi[i];
-        h[2] = S[i];
-        h[3] = a;
-        h[4] = b;
-        h[5] = ev;
-    };
-    auto dots = [&](int which, const double* a, const double* b, const double* cc) -> mem_status {
-        launch_dots(d, which, a, b, cc, c->dpart, c->dots, st);
-        c->launches += 2;
-        TRY(after_launch(c, "dot products"));
-        CK(cudaMemcpyAsync(hd.data(), c->dots, 2 * NI * sizeof(double), cudaMemcpyDeviceToHost, st), "dots");
-        CK(cudaStreamSynchronize(st), "dots sync");
-        return MEM_OK;
-    };
-    auto set_dev = [&](void* dst, const void* src, size_t bytes) -> mem_status {
-        CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "upload");
-        return MEM_OK;
-    };
-
-    launch_clip_f32_to_f64(d, image_dev_inout, c->I64, st);
-    c->launches++;
-    TRY(objgrad());
-    for (int i = 0; i < NI; ++i) put_hist(i, 0, 0.0, 0.0, 0.0);
-
-    int k_done = 0;
-    for (int k = 0; k < n_iter; ++k) {
-        bool any = false;
-        for (int i = 0; i < NI; ++i) any |= active[i] != 0;
-        if (!any) break;
-        // Polak-Ribiere beta (clipped at 0), restart every RESTART iterations
-        for (int i = 0; i < NI; ++i) beta[i] = 0.0;
-        if (k > 0 && k % RESTART != 0) {
-            TRY(dots(DOT_BETA, c->g64, c->gp64, nullptr));
-            for (int i = 0; i < NI; ++i) {
-                double gg = hd[2 * i], pr = hd[2 * i + 1];
-                if (gg > 0.0) beta[i] = std::max(0.0, pr / gg);
-            }
-        }
-        for (int i = 0; i < NI; ++i) mode[i] = active[i] ? (beta[i] == 0.0 ? 2 : 1) : 0;
-        TRY(set_dev(c->beta, beta.data(), NI * sizeof(double)));
-        TRY(set_dev(c->mode, mode.data(), NI * sizeof(int)));
-        launch_cg_direction(d, c->I64, c->g64, c->beta, c->mode, c->d64, st);
-        c->launches++;
-        TRY(dots(DOT_SLOPE, c->gf64, c->d64, c->g64));
-        bool need_restart = false;
-        for (int i = 0; i < NI; ++i) {
-            slope[i] = hd[2 * i];
-            mode[i] = 0;
-            if (active[i] && slope[i] >= 0.0) {
-                mode[i] = 2;
-                beta[i] = 0.0;
-                need_restart = true;
-            }
-        }
-        if (need_restart) {
-            TRY(set_dev(c->mode, mode.data(), NI * sizeof(int)));
-            launch_cg_direction(d, c->I64, c->g64, c->beta, c->mode, c->d64, st);
-            c->launches++;
-            TRY(dots(DOT_SLOPE, c->gf64, c->d64, c->g64));
-            for (int i = 0; i < NI; ++i)
-                if (mode[i] == 2) slope[i] = hd[2 * i];
-        }
-        for (int i = 0; i < NI; ++i)
-            if (active[i] && slope[i] >= 0.0) {
-                active[i] = 0;
-                stopped_early = 1;
-            }
-        // quadratic model of chi^2 along d: curvature sum w |F(A d)|^2
-        {
-            ImgSrc src{nullptr, c->d64, nullptr, nullptr, c->G, 0};
-            TRY(graphed(c, c->g_solve_curv, c->d64, nullptr, FWD_CURV,
-                        [&]() { return run_forward(c, src, FWD_CURV, false, nullptr); }));
-            TRY(read_scalars(c, sc));
-        }
-        std::vector<LineSearch> ls(NI);
-        std::vector<double> alpha0(NI, 0.0);
-        bool need_max = false;
-        for (int i = 0; i < NI; ++i) {
-            if (!active[i]) continue;
-            double curv = 2.0 * sc[4 + 3 * i];
-            if (curv > 0.0) alpha0[i] = -slope[i] / curv;
-            else need_max = true;
-        }
-        if (need_max) {
-            TRY(dots(DOT_MAX, c->I64, c->d64, nullptr));
-            for (int i = 0; i < NI; ++i)
-                if (active[i] && !(alpha0[i] > 0.0)) alpha0[i] = hd[2 * i] / hd[2 * i + 1];
-        }
-        for (int i = 0; i < NI; ++i)
-            if (active[i]) ls[i].start(phi[i], alpha0[i]);
-        // batched line searches: one objective evaluation serves every image
-        for (;;) {
-            bool running = false;
-            for (int i = 0; i < NI; ++i) {
-                alpha[i] = (active[i] && ls[i].running()) ? ls[i].req : 0.0;
-                running |= active[i] && ls[i].running();
-            }
-            if (!running) break;
-            TRY(set_dev(c->alpha, alpha.data(), NI * sizeof(double)));
-            // phi(alpha) = Phi(I) + [Phi(max(I + alpha d, G)) - Phi(I)], the change
-            // evaluated from the image difference so that its rounding error
-            // scales with the step, not with Phi
-            ImgSrc src{nullptr, c->I64, c->d64, c->alpha, c->G, 1};
-            void* ybuf = c->prec == MEM_PREC_FP64_DIRECT ? (void*)c->y64 : (void*)c->y32;
-            TRY(graphed(c, c->g_solve_probe, c->I64, c->d64, FWD_DCHI,
-                        [&]() { return run_forward(c, src, FWD_DCHI, true, ybuf); }));
-            TRY(read_scalars(c, sc));
-            for (int i = 0; i < NI; ++i)
-                if (active[i] && ls[i].running()) ls[i].feed(phi[i] + sc[3 + 3 * i]);
-        }
-        for (int i = 0; i < NI; ++i) {
-            alpha[i] = 0.0;
-            if (!active[i]) continue;
-            if (ls[i].alpha <= 0.0) {
-                active[i] = 0;
-                stopped_early = 1;
-                continue;
-            }
-            alpha[i] = ls[i].alpha;
-        }
-        TRY(set_dev(c->alpha, alpha.data(), NI * sizeof(double)));
-        launch_cg_step(d, c->I64, c->d64, c->alpha, st);
-        CK(cudaMemcpyAsync(c->gp64, c->g64, n * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy g");
-        c->launches++;
-        std::vector<double> phi_old = phi, chi_old = chi, S_old = S;
-        TRY(objgrad());
-        for (int i = 0; i < NI; ++i) {
-            if (alpha[i] > 0.0) {
-                iters[i] = k + 1;
-                evals_tot[i] += ls[i].evals + 2;
-                put_hist(i, k + 1, alpha[i], beta[i], (double)(ls[i].evals + 2));
-            } else {
-                phi[i] = phi_old[i];
-                chi[i] = chi_old[i];
-                S[i] = S_old[i];
-                put_hist(i, k + 1, 0.0, 0.0, 0.0);
-            }
-        }
-        k_done = k + 1;
+    TRY(dalloc(c, &c->cg_st, (size_t)NI));
+    TRY(dalloc(c, &c->cg_ctl, (size_t)1));
+    const size_t hist_n = (size_t)NI * (n_iter + 1) * 6;
+    if (hist_n > c->cg_hist_cap) {
+        // grow: the old block stays allocated until destroy; the solve graph
+        // refers to the history buffer and is rebuilt
+        c->cg_hist = nullptr;
+        TRY(dalloc(c, &c->cg_hist, std::max(hist_n, (size_t)NI * 51 * 6)));
+        c->cg_hist_cap = std::max(hist_n, (size_t)NI * 51 * 6);
     }
-    for (int k = k_done + 1; k <= n_iter; ++k)
-        for (int i = 0; i < NI; ++i) put_hist(i, k, 0.0, 0.0, 0.0);
+    cudaStream_t st = c->st;
+    CgControl h0;
+    std::memset(&h0, 0, sizeof h0);
+    h0.n_iter = n_iter;
+    h0.hist_stride = n_iter + 1;
+    CK(cudaMemcpyAsync(c->cg_ctl, &h0, sizeof h0, cudaMemcpyHostToDevice, st), "solver control");
+    launch_clip_f32_to_f64(c->dd(), image_dev_inout, c->I64, st);
+    c->launches++;
+    TRY(after_launch(c, "image upload"));
+
+    CgControl hc;
+    if (c->graphs && !c->profiling) {
+        if (!(c->g_solve.exec && c->g_solve.prec == c->prec && c->g_solve.hist == c->cg_hist))
+            TRY(build_solve_graph(c));
+        CK(cudaGraphLaunch(c->g_solve.exec, st), "solve graph launch");
+        CK(cudaMemcpyAsync(&hc, c->cg_ctl, sizeof hc, cudaMemcpyDeviceToHost, st), "solver control");
+        CK(cudaStreamSynchronize(st), "solve");
+        c->launches += c->g_solve.n_pro + (int64_t)hc.k * c->g_solve.n_iter + hc.probes * c->g_solve.n_probe;
+    } else {
+        // the same launch sequence, the loops driven from the host
+        auto read_ctl = [&]() -> mem_status {
+            CK(cudaMemcpyAsync(&hc, c->cg_ctl, sizeof hc, cudaMemcpyDeviceToHost, st), "solver control");
+            CK(cudaStreamSynchronize(st), "solver control");
+            return MEM_OK;
+        };
+        TRY(solve_prologue(c, 0));
+        for (;;) {
+            TRY(read_ctl());
+            if (!hc.outer) break;
+            TRY(solve_iter_head(c, 0));
+            for (;;) {
+                TRY(read_ctl());
+                if (!hc.inner) break;
+                TRY(solve_probe(c, 0));
+            }
+            TRY(solve_iter_tail(c, 0));
+        }
+    }
     launch_f64_to_f32((int64_t)n, c->I64, image_dev_inout, st);
     c->launches++;
     TRY(after_launch(c, "image download"));
+    std::vector<CgImage> cg(NI);
+    std::vector<double> hist((size_t)NI * (n_iter + 1) * 6, 0.0);
+    CK(cudaMemcpyAsync(cg.data(), c->cg_st, NI * sizeof(CgImage), cudaMemcpyDeviceToHost, st), "solver state");
+    CK(cudaMemcpyAsync(hist.data(), c->cg_hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "solver history");
     TRY(check_status(c));
+    if (hc.status & CG_NONFINITE) return fail(c, MEM_ENUMERIC, "objective is not finite (pixels <= 0?)");
+    if (hc.status & CG_LOOP) return fail(c, MEM_ENUMERIC, "a line search did not end within its evaluation budget");
+    // rows after the last iteration repeat the final objective
+    for (int i = 0; i < NI; ++i)
+        for (int k = hc.k + 1; k <= n_iter; ++k) {
+            double* r = &hist[((size_t)i * (n_iter + 1) + k) * 6];
+            r[0] = cg[i].phi;
+            r[1] = cg[i].chi;
+            r[2] = cg[i].S;
+            r[3] = r[4] = r[5] = 0.0;
+        }
     if (hist_host) std::memcpy(hist_host, hist.data(), hist.size() * sizeof(double));
     if (rep) {
-        rep->iterations = *std::max_element(iters.begin(), iters.end());
+        rep->iterations = 0;
         rep->evaluations = 0;
-        for (int x : evals_tot) rep->evaluations += x;
         rep->status = MEM_OK;
-        rep->stopped_early = stopped_early;
+        rep->stopped_early = hc.stopped_early;
         rep->phi = rep->chi2 = rep->entropy = 0.0;
         for (int i = 0; i < NI; ++i) {
-            rep->phi += phi[i];
-            rep->chi2 += chi[i];
-            rep->entropy += S[i];
+            rep->iterations = std::max(rep->iterations, cg[i].iters);
+            rep->evaluations += cg[i].evals;
+            rep->phi += cg[i].phi;
+            rep->chi2 += cg[i].chi;
+            rep->entropy += cg[i].S;
         }
     }
     return MEM_OK;

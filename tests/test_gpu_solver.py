@@ -148,3 +148,50 @@ def test_autograd_fp64_gradcheck_style(ms, oracle_mod):
     g = img.grad.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(g - rg) / np.linalg.norm(rg) <= 1e-5
     ctx.close()
+
+
+@pytest.mark.parametrize("form", ["fp16x3", "fp64_direct"])
+def test_solve_graph_and_host_driven_loops_agree(ms, form):
+    """The solve runs as one CUDA graph whose iteration and line-search loops
+    are conditional WHILE nodes steered by device-side controller kernels.
+    With graphs off, the host drives the same loops over the same launches
+    (reading the loop conditions back each probe): the results agree bit for
+    bit, for a single image and for a cube with an empty channel."""
+    import torch
+    for ds, n_iter in [(S.make(1), 12),
+                       (S.random_problem(64, 0, seed=32, C=3, z_list=[300, 0, 200], lam=20.0, G=1e-3), 6)]:
+        I0 = torch.full((ds.C if not ds.shared_image else 1, ds.N, ds.N), float(np.float32(ds.G)),
+                        dtype=torch.float32, device="cuda")
+        out = []
+        for graphs in (True, False):
+            ctx = ms.Context(ds, precision=form)
+            ms.mem_use_graphs(ctx.handle, graphs)
+            img, rep, hist = ctx.solve(I0, n_iter)
+            out.append((img.cpu().numpy(), rep.iterations, rep.evaluations, rep.phi, hist))
+            ctx.close()
+        (a, ia, ea, pa, ha), (b, ib, eb, pb, hb) = out
+        assert np.array_equal(a, b)
+        assert (ia, ea, pa) == (ib, eb, pb)
+        assert np.array_equal(ha, hb)
+        assert ia == n_iter
+
+
+def test_solve_timeout_is_reported_and_device_stays_usable(ms, oracle_mod):
+    """A bounded device-side wait that runs out inside a solve stops the
+    device-side loops (the controllers read the status word) and the call
+    returns MEM_ETIMEOUT; a fresh context then solves normally."""
+    import torch
+    ds = S.random_problem(128, 2000, 84, lam=1.0)
+    I0 = torch.full((1, ds.N, ds.N), float(np.float32(ds.G)), dtype=torch.float32, device="cuda")
+    bad = ms.Context(ds, precision="fp16x3", spin_limit=1)
+    with pytest.raises(ms.MemError) as e:
+        bad.solve(I0, 5)
+    assert e.value.status == 4
+    bad.close()
+    good = ms.Context(ds, precision="fp16x3")
+    img, rep, hist = good.solve(I0, 5)
+    good.close()
+    assert rep.iterations == 5
+    P = oracle_mod.Problem.from_dataset(ds)
+    own = oracle_mod.objective(P, img.cpu().numpy().astype(np.float64))[0]
+    assert abs(rep.phi - own) <= 1e-5 * abs(own)
