@@ -144,8 +144,9 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                             const uint64_t b_h = smem_desc(B + bo, lboB, 128);
                             const uint64_t b_l = smem_desc(B + BN * TC_BK * 2 + bo, lboB, 128);
                             const uint32_t acc = (ks > ks0 || kk > 0) ? 1u : 0u;
-                            umma_bf16(dt, a_h, b_h, idesc, acc);
-                            umma_bf16(dt, a_h, b_l, idesc, 1u);
+                            // hi x hi and hi x lo share the A tile: one read
+                            umma_f16_collect<COLLECT_FILL>(dt, a_h, b_h, idesc, acc);
+                            umma_f16_collect<COLLECT_LASTUSE>(dt, a_h, b_l, idesc, 1u);
                             umma_bf16(dt, a_l, b_h, idesc, 1u);
                         }
                         umma_commit(&S.empty[s]);

@@ -201,11 +201,12 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                         const uint64_t aim_l = smem_desc(A + 3 * a_plane + ao, lboA, 128);
                         const uint32_t dt = tmem + (uint32_t)(mt * BLK);
                         const uint32_t acc = ks > seg0 ? 1u : 0u;
-                        umma_bf16(dt, are_h, bre_h, idesc, acc);
-                        umma_bf16(dt, are_h, bre_l, idesc, 1u);
+                        // products sharing an A tile read it once (collector buffer)
+                        umma_f16_collect<COLLECT_FILL>(dt, are_h, bre_h, idesc, acc);
+                        umma_f16_collect<COLLECT_LASTUSE>(dt, are_h, bre_l, idesc, 1u);
                         umma_bf16(dt, are_l, bre_h, idesc, 1u);
-                        umma_bf16(dt, aim_h, bim_h, idesc, 1u);
-                        umma_bf16(dt, aim_h, bim_l, idesc, 1u);
+                        umma_f16_collect<COLLECT_FILL>(dt, aim_h, bim_h, idesc, 1u);
+                        umma_f16_collect<COLLECT_LASTUSE>(dt, aim_h, bim_l, idesc, 1u);
                         umma_bf16(dt, aim_l, bim_h, idesc, 1u);
                     }
                     umma_commit(&S.empty[s]);
