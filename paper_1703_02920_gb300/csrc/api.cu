@@ -12,7 +12,6 @@
 #include <string>
 #include <vector>
 
-#include <cufft.h>
 #include <sys/stat.h>
 
 #include "../../include/libmemsynth.h"
@@ -113,14 +112,12 @@ struct mem_ctx {
     int fwd_kernel = MEM_FWD_STREAM, fwd_bn = 0, fwd_stages = 4, adj_stages = 3;
     double2* vpart = nullptr;  // resident kernel: slice partials [slice][Z]
 
-    // gridded forward (the paper's FFT + bilinear approximation): padded
-    // images and their half spectra, and the batched cuFFT plan for `grid_pad`
+    // gridded forward (the paper's FFT + bilinear approximation): row
+    // spectra and 2-D half spectra for `grid_pad`
     std::vector<double> wsum_h;   // per-channel sum of weights (natural-weights dirty image)
     double* wsum = nullptr;
     int grid_pad = 0;
-    bool grid_plan_ok = false;
-    cufftHandle grid_plan = 0;
-    float* grid_P = nullptr;
+    float2* grid_R = nullptr;
     float2* grid_F = nullptr;
     std::string gpu_name;
 
@@ -1008,37 +1005,29 @@ mem_status mem_forward_gridded(mem_ctx* c, const float* image_dev, int32_t pad, 
     if (!c || !image_dev || (!vis_dev && c->Z > 0)) return fail(c, MEM_EINVAL, "null argument");
     if (pad < 1 || pad > 8) return fail(c, MEM_EINVAL, "gridded forward: pad must be 1..8 (got %d)", pad);
     const int M = pad * c->N;
-    const size_t MM = (size_t)M * M, H = (size_t)M * (M / 2 + 1);
+    if (!grid_fft_size_ok(c->N, M))
+        return fail(c, MEM_EINVAL, "gridded forward: needs an even N and pad * N <= %d (N = %d, pad = %d)",
+                    GRID_FFT_MAX, c->N, pad);
+    const size_t H = (size_t)M / 2 + 1;
     if (c->grid_pad != pad) {
         TRY(mem_sync(c));
-        if (c->grid_plan_ok) cufftDestroy(c->grid_plan);
-        c->grid_plan_ok = false;
-        dfree(c, &c->grid_P, (size_t)c->C * (size_t)(c->grid_pad * c->N) * (size_t)(c->grid_pad * c->N));
-        const size_t oldM = (size_t)c->grid_pad * c->N;
-        dfree(c, &c->grid_F, (size_t)c->C * oldM * (oldM / 2 + 1));
+        if (c->grid_pad) {
+            const size_t oM = (size_t)c->grid_pad * c->N, oH = oM / 2 + 1;
+            dfree(c, &c->grid_R, (size_t)c->C * oH * c->N);
+            dfree(c, &c->grid_F, (size_t)c->C * oM * oH);
+        }
         c->grid_pad = 0;
-        TRY(dalloc(c, &c->grid_P, (size_t)c->C * MM));
-        TRY(dalloc(c, &c->grid_F, (size_t)c->C * H));
-        int n[2] = {M, M};
-        if (cufftPlanMany(&c->grid_plan, 2, n, nullptr, 1, (int)MM, nullptr, 1, (int)H, CUFFT_R2C, c->C) !=
-            CUFFT_SUCCESS)
-            return fail(c, MEM_ECUDA, "cuFFT plan for the gridded forward (M = %d, %d channels)", M, c->C);
-        c->grid_plan_ok = true;
+        TRY(dalloc(c, &c->grid_R, (size_t)c->C * H * c->N));
+        TRY(dalloc(c, &c->grid_F, (size_t)c->C * M * H));
         c->grid_pad = pad;
     }
-    if (cufftSetStream(c->grid_plan, c->st) != CUFFT_SUCCESS) return fail(c, MEM_ECUDA, "cuFFT stream");
     DevData d = c->dd();
     {
-        KTimer t(c, "grid_pad");
-        launch_grid_pad(d, image_dev, M, c->grid_P, c->st);
-        c->launches++;
-    }
-    TRY(after_launch(c, "gridded forward: padding"));
-    {
         KTimer t(c, "grid_fft");
-        if (cufftExecR2C(c->grid_plan, (cufftReal*)c->grid_P, (cufftComplex*)c->grid_F) != CUFFT_SUCCESS)
-            return fail(c, MEM_ECUDA, "cuFFT R2C execution");
+        launch_grid_fft(d, image_dev, M, c->grid_R, c->grid_F, c->st);
+        c->launches += 2;
     }
+    TRY(after_launch(c, "gridded forward: 2-D transform"));
     {
         KTimer t(c, "grid_interp");
         launch_grid_interp(d, M, c->grid_F, c->Z, (float2*)vis_dev, c->st);
@@ -1185,7 +1174,6 @@ void mem_destroy(mem_ctx* c) {
         cudaEventDestroy(k.b);
     }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
-    if (c->grid_plan_ok) cufftDestroy(c->grid_plan);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }

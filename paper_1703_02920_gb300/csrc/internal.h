@@ -120,16 +120,20 @@ int fwd_tc_smem_bytes(int N, int BN, int stages);
 // kernel that also applies the forward mode.
 __host__ __device__ inline int fwd_rs_ks(int N) { return N < 128 ? N : 128; }
 int fwd_rs_smem_bytes(int N, int stages);
-// The paper's gridded forward: padding (M = pad N, image centred) and the
-// modulated bilinear interpolation of the batched R2C half spectra.
-void launch_grid_pad(const DevData& d, const float* img, int M, float* P, cudaStream_t st);
+// The paper's gridded forward: the 2-D real-to-complex transform of every
+// channel's A_c * I zero-padded to M x M (image centred), as this library's
+// own FFT kernels (rows into R[C][M/2+1][N], columns into F[C][M][M/2+1]),
+// then the modulated bilinear interpolation of the half spectra.
+constexpr int GRID_FFT_MAX = 8192;  // M <= 8192: two M-point buffers per CTA in shared memory
+bool grid_fft_size_ok(int N, int M);  // N even, M = 2^a q with q in {1, 3, 5, 7}, M <= GRID_FFT_MAX
+void launch_grid_fft(const DevData& d, const float* img, int M, float2* R, float2* F, cudaStream_t st);
 // Dirty image / PSF / residual map: weighted adjoint inputs (what: 0 data,
 // 1 PSF, 2 residuals against the model in y32 / y64), and the per-channel
 // image from the adjoint's FP64 sums (no primary-beam factor).
 void launch_dirty_y(const DevData& d, const double* wsum, int what, int64_t z_total, float2* y32, double2* y64,
                     cudaStream_t st);
 void launch_dirty_out(const DevData& d, const double* gsum, int ks, float* out, cudaStream_t st);
-void launch_grid_interp(const DevData& d, int M, const void* F, int64_t z_total, float2* vis, cudaStream_t st);
+void launch_grid_interp(const DevData& d, int M, const float2* F, int64_t z_total, float2* vis, cudaStream_t st);
 int fwd_rs_max_stages(int N);
 void launch_fwd_rs(const DevData& d, int f16, const VisTile* tiles, int n_tiles, const void* planes,
                    const float* cmean, const float* cscale, int mode, float2* yout, double* chi_part,

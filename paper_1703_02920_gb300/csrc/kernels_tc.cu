@@ -221,14 +221,22 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
         __syncwarp();
     } else {
         // ------------------------------------------ producers (13 warps, 416 thr)
-        const int ptid = threadIdx.x - (warp > 4 ? 32 : 0);
-        const int n_groups = ADJ_PRODUCER_WARPS * 2;  // 16-thread groups, one item each
-        // half of the groups write Ey items (A operand), half P items (B operand),
-        // so that each thread builds one step table per stage
-        const bool ey_side = (ptid >> 4) < n_groups / 2;
-        const int side_grp = ey_side ? (ptid >> 4) : (ptid >> 4) - n_groups / 2;
-        const int jj = ptid & 15;           // visibility within the stage
+        // A warp-iteration builds two items (8 pixels of 16 visibilities each,
+        // one per half-warp).  Whole warps take one side, Ey items (A operand)
+        // or P items (B operand), so each thread builds one step table per
+        // stage and the halves of a warp never diverge.  A stage has 16
+        // warp-iterations per side (N >= 256); the table gives each warp a
+        // contiguous run of them such that every SM sub-partition (warp % 4;
+        // their FMA pipes are the busy units) carries 8 per stage and no warp
+        // more than 3.  Smaller images use the runs' first entries.
+        const int pw = warp < 4 ? warp : warp - 1;  // producer warp 0..12
+        const int ey_side = (0x3F >> pw) & 1;       // warps 0-3, 5, 6
+        const int wi_start = (int)((0xA6EC8039E63C0ull >> (4 * pw)) & 15);
+        const int wi_cap = (int)((0x2222233323323ull >> (4 * pw)) & 15);
+        const int half = lane >> 4;
+        const int jj = lane & 15;           // visibility within the stage
         const int ngA = R / 8, ngB = BLK / 8;
+        const int wi_end = min(wi_start + wi_cap, (ey_side ? ngA : ngB) / 2);
         const float ysc = F16 ? pow2_scale_for(ymax[0]) : 1.f;
         uint32_t sc = 0, dr = 0;  // stages produced; accumulator drains (warps 0-3)
         bool ok = true;
@@ -281,8 +289,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                 if (!ok) break;
                 unsigned char* A = smem + s * stage_bytes;
                 unsigned char* B = A + 4 * a_plane;
-                for (int it2 = side_grp; it2 < (ey_side ? ngA : ngB); it2 += n_groups / 2) {
-                    const int item = ey_side ? it2 : ngA + it2;
+                for (int wi = wi_start; wi < wi_end; ++wi) {
+                    const int item = ey_side ? 2 * wi + half : ngA + 2 * wi + half;
                     uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
                     unsigned char* dst;
                     int plane;
