@@ -46,6 +46,9 @@ constexpr int F2_THREADS = 448;
 constexpr int F2_APLANE = 128 * TC_BK * 2;  // bytes of one A plane (hi or lo), 8 KB
 constexpr int F2_ABYTES = 2 * F2_APLANE;
 constexpr int F2_KSEG = 256;                 // image rows per accumulation (at most)
+// Phase factors advanced by complex recurrence (one product each) between
+// SFU evaluations, which are taken every PHASE_REFRESH steps.
+constexpr int PHASE_REFRESH = 4;
 
 __host__ __device__ inline int f2_stage_bytes(int BN) { return F2_ABYTES + 2 * BN * TC_BK * 2; }
 __host__ __device__ inline uint32_t f2_tmem_cols(int BN) {
@@ -211,14 +214,21 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
 #pragma unroll
             for (int q = 0; q < 8; ++q) step[q] = cis_neg(phase_mul(q, pb));
             const Rot8 w = rot8_of(step);
+            // the group's first row advances by TC_BK rows per stage: its phase
+            // factor is the previous one times exp(-2 pi i TC_BK b), refreshed
+            // from the SFU every PHASE_REFRESH stages (the products' rounding is
+            // unbiased and does not accumulate further)
+            const cf2 step_bk = cis_neg(phase_mul(TC_BK, pb));
             for (int mb = 0; mb < n_mb && ok; ++mb) {
+                cf2 base = {1.f, 0.f};
                 for (int ks = 0; ks < nk; ++ks, ++sc) {
                     const int s = sc % F2_STAGES;
                     // the table values need no ring slot: compute them, then wait
                     uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
                     if (valid) {
                         const int n0 = ks * TC_BK + g * 8;
-                        table8_split<F16>(cis_neg(phase_mul(n0 - c0, pb)), w, rh, rl, ih, il);
+                        base = (ks % PHASE_REFRESH) ? cmul(base, step_bk) : cis_neg(phase_mul(n0 - c0, pb));
+                        table8_split<F16>(base, w, rh, rl, ih, il);
                     }
                     ok = __all_sync(0xffffffffu, mbar_wait(&S.empty[s], ((sc / F2_STAGES) & 1) ^ 1, spin,
                                                            abort, status, 64));
@@ -279,6 +289,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             for (int q = 0; q < 8; ++q) step[q] = cis_neg(phase_mul(q, pa));
             const Rot8 wx8 = rot8_of(step);
             const cf2 step8 = cis_neg(phase_mul(8, pa));
+            const cf2 step16 = cis_neg(phase_mul(16, pa));  // chunk to chunk (recurrence below)
             // this lane's component of S_j = sum_n Ey[j,n] (accurate sincospi of
             // the exact half-turn and N/2-multiple phases)
             float scomp;
@@ -311,9 +322,14 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                 uint32_t tv[2][16];
                 auto load_chunk = [&](int q, int slot) { tmem_ld16(lane_base + q * 16, tv[slot]); };
                 // sum_k Ex[m0+k] t_k = base * sum_{k<8} step_k t_k + base8 * sum_{k<8} step_k t_{k+8}
+                // the chunk's phase factor exp(-2 pi i (m0 - N/2) a): the previous
+                // chunk's times step16, refreshed from the SFU every
+                // PHASE_REFRESH chunks (chunks run in order)
+                cf2 ebase = {1.f, 0.f};
                 auto reduce_chunk = [&](int q, int slot) {
                     const int m0 = mb * BN + q * 16;
-                    const cf2 base = cis_neg(phase_mul(m0 - c0, pa));
+                    const cf2 base = (q % PHASE_REFRESH) ? cmul(ebase, step16) : cis_neg(phase_mul(m0 - c0, pa));
+                    ebase = base;
                     const cf2 base8 = cmul(base, step8);
                     float2 cq[8];
 #pragma unroll

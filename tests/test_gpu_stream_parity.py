@@ -32,7 +32,8 @@ FORMS = ["fp16x3", "bf16x3"]
 TOL_PHI_FINAL = {"fp16x3": 1e-6, "bf16x3": 3e-6}
 # the 40-iteration trajectory is far from converged and amplifies evaluation
 # errors (a 1e-7 max|V| perturbation of the oracle's own forward moves the
-# config-1 final objective by 6e-5); BF16x3's errors are about 10x FP16x3's
+# config-1 final objective by 6e-5); BF16x3's errors are about 10x FP16x3's.
+# One-sided: the form's objective must have fallen at least about as far.
 TRAJ_PHI = {"fp16x3": 2e-5, "bf16x3": 1e-4}
 TOL_CHI = {"fp16x3": 3e-6, "bf16x3": 1e-5}
 TOL_V = 1e-5
@@ -82,9 +83,11 @@ def test_stream_solve_256_matches_oracle(ms, solve256, oracle_mod, form):
     assert rel <= 1e-3, rel
     own_phi, own_chi, _ = oracle_mod.objective(P, img)
     assert abs(rep.phi - own_phi) <= TOL_PHI_FINAL[form] * abs(own_phi), (rep.phi, own_phi)
-    # and along the way the objective fell as far as the oracle's did
+    # and along the way the objective fell at least as far as the oracle's did
+    # (an unconverged trajectory may well end lower: its own objective at its
+    # own image is checked above)
     ref_phi = ref_hist[-1]["phi"]
-    assert abs(rep.phi - ref_phi) <= TRAJ_PHI[form] * abs(ref_phi), (rep.phi, ref_phi)
+    assert rep.phi - ref_phi <= TRAJ_PHI[form] * abs(ref_phi), (rep.phi, ref_phi)
 
 
 def _cases():
