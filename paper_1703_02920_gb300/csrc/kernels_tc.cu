@@ -289,7 +289,12 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                 if (!ok) break;
                 unsigned char* A = smem + s * stage_bytes;
                 unsigned char* B = A + 4 * a_plane;
-                for (int wi = wi_start; wi < wi_end; ++wi) {
+                // at most 3 warp-iterations (the table): unrolled so that the
+                // items' independent arithmetic interleaves
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    const int wi = wi_start + r;
+                    if (wi >= wi_end) break;
                     const int item = ey_side ? 2 * wi + half : ngA + 2 * wi + half;
                     uint4 rh = {0, 0, 0, 0}, rl = {0, 0, 0, 0}, ih = {0, 0, 0, 0}, il = {0, 0, 0, 0};
                     unsigned char* dst;
