@@ -59,8 +59,8 @@ __host__ __device__ inline uint32_t f2_tmem_cols(int BN) {
 
 
 struct F2Shared {
-    uint64_t full[F2_MAX_STAGES];   // producer warps (8 arrivals)
-    uint64_t bfull[F2_MAX_STAGES];  // image operand bulk copy (transaction bytes)
+    uint64_t full[F2_MAX_STAGES];   // producer warps (8 arrivals) + the copy warp once the stage's image chunk landed
+    uint64_t bfull[F2_MAX_STAGES];  // image operand bulk copy (transaction bytes; watched by the copy warp)
     uint64_t empty[F2_MAX_STAGES];  // MMA completion (tcgen05.commit)
     uint64_t tfull[2];
     uint64_t tempty[2];         // 4 epilogue warps
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < F2_STAGES; ++s) {
-            mbar_init(&S.full[s], 8);
+            mbar_init(&S.full[s], 9);
             mbar_init(&S.bfull[s], 1);
             mbar_init(&S.empty[s], 1);
         }
@@ -121,6 +121,13 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             const uint32_t idesc = idesc_f16kind(128, BN, 0, 0, F16 ? 0 : 1);
             const uint32_t sbase = smem_u32(smem);
             const uint32_t lboB = (uint32_t)(BN / 8) * 128;
+            // Operand descriptors of slot 0; another slot or K step only moves
+            // the start address, whose field (address >> 4, low 14 bits) takes
+            // the offset by plain addition (shared memory < 256 KB, no carry).
+            const uint64_t d_ah = smem_desc(sbase, 2048, 128);
+            const uint64_t d_al = smem_desc(sbase + F2_APLANE, 2048, 128);
+            const uint64_t d_bh = smem_desc(sbase + F2_ABYTES, lboB, 128);
+            const uint64_t d_bl = smem_desc(sbase + F2_ABYTES + BN * TC_BK * 2, lboB, 128);
             uint32_t sc = 0, it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
@@ -133,19 +140,17 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                     const uint32_t dt = tmem + (uint32_t)(b * BN);
                     for (int ks = ks0; ks < ks0 + kseg; ++ks, ++sc) {
                         const int s = sc % F2_STAGES;
-                        ok = mbar_wait(&S.full[s], (sc / F2_STAGES) & 1, spin, abort, status) &&
-                             mbar_wait(&S.bfull[s], (sc / F2_STAGES) & 1, spin, abort, status);
+                        // one wait: the producers' tables and the image chunk
+                        ok = mbar_wait(&S.full[s], (sc / F2_STAGES) & 1, spin, abort, status);
                         if (!ok) break;
                         tc_fence_after();
-                        const uint32_t A = sbase + s * stage_bytes;
-                        const uint32_t B = A + F2_ABYTES;
+                        const uint64_t so = (uint64_t)((uint32_t)(s * stage_bytes) >> 4);
 #pragma unroll
                         for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                            const uint32_t ao = kk * 2 * 2048, bo = kk * 2 * lboB;
-                            const uint64_t a_h = smem_desc(A + ao, 2048, 128);
-                            const uint64_t a_l = smem_desc(A + F2_APLANE + ao, 2048, 128);
-                            const uint64_t b_h = smem_desc(B + bo, lboB, 128);
-                            const uint64_t b_l = smem_desc(B + BN * TC_BK * 2 + bo, lboB, 128);
+                            const uint64_t ao = so + (uint64_t)(kk * 2 * 2048 >> 4);
+                            const uint64_t bo = so + (uint64_t)(kk * 2 * lboB >> 4);
+                            const uint64_t a_h = d_ah + ao, a_l = d_al + ao;
+                            const uint64_t b_h = d_bh + bo, b_l = d_bl + bo;
                             const uint32_t acc = (ks > ks0 || kk > 0) ? 1u : 0u;
                             // hi x hi and hi x lo share the A tile: one read
                             umma_f16_collect<COLLECT_FILL>(dt, a_h, b_h, idesc, acc);
@@ -170,6 +175,14 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
             uint32_t sc = 0;
             bool ok = true;
             const uint32_t chunk_bytes = 2u * BN * TC_BK * 2;
+            // once stage q's chunk has landed (bfull), the copy warp is the
+            // ninth arrival on full[q]; it does so one stage behind the copy it
+            // issues, so that a copy is always in flight
+            auto land = [&](uint32_t q) -> bool {
+                if (!mbar_wait(&S.bfull[q % F2_STAGES], (q / F2_STAGES) & 1, spin, abort, status)) return false;
+                mbar_arrive(&S.full[q % F2_STAGES]);
+                return true;
+            };
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int chan = tiles[t].chan;
                 const unsigned char* cbase = (const unsigned char*)(planes + (int64_t)chan * 2 * NN);  // 16-bit elements
@@ -181,9 +194,17 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
                         mbar_arrive_expect_tx(&S.bfull[s], chunk_bytes);
                         bulk_g2s(smem + s * stage_bytes + F2_ABYTES,
                                  cbase + (int64_t)(mb * nk + ks) * chunk_bytes, chunk_bytes, &S.bfull[s]);
+                        if (sc > 0) {
+                            ok = land(sc - 1);
+                            if (!ok) {
+                                ++sc;  // the copy just issued is in flight too
+                                break;
+                            }
+                        }
                     }
                 }
             }
+            if (ok && sc > 0) ok = land(sc - 1);
             if (!ok) {
                 // copies already issued land on their own; wait for them before
                 // the CTA's shared memory is released

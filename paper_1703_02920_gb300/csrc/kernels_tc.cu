@@ -171,6 +171,15 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
         if (lane == 0) {
             const uint32_t idesc = idesc_f16kind(128, BLK, 1, 1, F16 ? 0 : 1);
             const uint32_t sbase = smem_u32(smem);
+            const uint32_t lboA = (uint32_t)(R / 8) * 128, lboB = (uint32_t)(BLK / 8) * 128;
+            // Operand descriptors of slot 0; another slot or row block only
+            // moves the start address, whose field (address >> 4, low 14 bits)
+            // takes the offset by plain addition (shared memory < 256 KB).
+            // (the four planes of an operand share their strides: plane i is
+            // plane 0 moved by i planes)
+            const uint64_t d_a = smem_desc(sbase, lboA, 128);
+            const uint64_t d_b = smem_desc(sbase + 4 * a_plane, lboB, 128);
+            const uint64_t pa16 = (uint64_t)(a_plane >> 4), pb16 = (uint64_t)(b_plane >> 4);
             uint32_t sc = 0;
             bool ok = true;
             uint32_t it = 0;  // accumulation segments so far (tfull / tempty phases)
@@ -186,19 +195,12 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                     ok = mbar_wait(&S.full[s], (sc / ADJ_STAGES) & 1, spin, abort, status);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t A = sbase + s * stage_bytes;
-                    const uint32_t B = A + 4 * a_plane;
-                    const uint32_t lboA = (uint32_t)(R / 8) * 128, lboB = (uint32_t)(BLK / 8) * 128;
-                    const uint64_t bre_h = smem_desc(B + 0 * b_plane, lboB, 128);
-                    const uint64_t bre_l = smem_desc(B + 1 * b_plane, lboB, 128);
-                    const uint64_t bim_h = smem_desc(B + 2 * b_plane, lboB, 128);
-                    const uint64_t bim_l = smem_desc(B + 3 * b_plane, lboB, 128);
+                    const uint64_t so = (uint64_t)((uint32_t)(s * stage_bytes) >> 4);
+                    const uint64_t bre_h = d_b + so, bre_l = bre_h + pb16;
+                    const uint64_t bim_h = bre_h + 2 * pb16, bim_l = bre_h + 3 * pb16;
                     for (int mt = 0; mt < n_mt; ++mt) {
-                        const uint32_t ao = mt * 2048;  // 16 groups of 8 rows
-                        const uint64_t are_h = smem_desc(A + 0 * a_plane + ao, lboA, 128);
-                        const uint64_t are_l = smem_desc(A + 1 * a_plane + ao, lboA, 128);
-                        const uint64_t aim_h = smem_desc(A + 2 * a_plane + ao, lboA, 128);
-                        const uint64_t aim_l = smem_desc(A + 3 * a_plane + ao, lboA, 128);
+                        const uint64_t are_h = d_a + so + (uint64_t)(mt * 2048 >> 4);  // 16 groups of 8 rows
+                        const uint64_t are_l = are_h + pa16, aim_h = are_h + 2 * pa16, aim_l = are_h + 3 * pa16;
                         const uint32_t dt = tmem + (uint32_t)(mt * BLK);
                         const uint32_t acc = ks > seg0 ? 1u : 0u;
                         // products sharing an A tile read it once (collector buffer)
