@@ -53,6 +53,21 @@ def test_gridded_forward_matches_oracle(ms, oracle_mod, pad, ci):
     ctx.close()
 
 
+@pytest.mark.parametrize("N,pad,Z", [(64, 5, 500), (64, 7, 500), (128, 6, 400), (256, 4, 600)])
+def test_gridded_forward_every_radix_and_large_grids(ms, oracle_mod, N, pad, Z):
+    """The transform's radix-5 and radix-7 stages (pad 5, 7), radix 3 with
+    radix 2 and 4 (pad 6) and a 1024-point grid (N = 256, pad 4) against the
+    oracle's statement of the same steps."""
+    import torch
+    ds = S.random_problem(N, Z, 86 + pad, C=1)
+    ctx = ms.Context(ds, precision="fp16x3")
+    V = ctx.forward_gridded(torch.from_numpy(ds.truth).cuda(), pad).cpu().numpy().astype(np.float64)
+    ref = _oracle_gridded(oracle_mod, ds, ds.truth, pad)
+    got = V[:, 0] + 1j * V[:, 1]
+    assert np.max(np.abs(got - ref)) <= 2e-5 * np.max(np.abs(ref)), (N, pad)
+    ctx.close()
+
+
 def test_gridded_forward_rejects_bad_pad(ms):
     import torch
     ds = S.random_problem(64, 10, 84)
