@@ -436,47 +436,76 @@ void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partia
 
 // Sum the unit partials of each (channel, block) in unit order (compensated
 // FP32, stored as FP64) into gsum[c][N*N] (without the beam factor).
-__global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __restrict__ cb_unit_off,
-                                                       const float* __restrict__ partial,
-                                                       const float* __restrict__ ymax,
-                                                       double* __restrict__ gsum) {
-    const int N = d.N;
-    const int64_t NN = (int64_t)N * N;
-    const int BLK = N < 256 ? N : 256;
-    const int nbx = N / BLK;
-    const int c = blockIdx.y;
-    // threads run over the partials' layout (coalesced reads); p is the pixel
-    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (i >= NN) return;
-    const int blk = (int)(i / ((int64_t)BLK * BLK));
-    const int64_t loc = i % ((int64_t)BLK * BLK);
-    int nl, ml;
-    adj_partial_rc(loc, BLK, nl, ml);
-    const int64_t p = (int64_t)((blk / nbx) * BLK + nl) * N + (blk % nbx) * BLK + ml;
-    const int cb = c * nbx * nbx + blk;
-    const int u0 = cb_unit_off[cb], u1 = cb_unit_off[cb + 1];
-    const int64_t stride = (int64_t)BLK * BLK;
-    const float* src = partial + loc;
-    // compensated FP32 sum in unit order (Neumaier); FP64 throughput on this
-    // part is too low for one FP64 add per partial
-    float s = 0.f, comp = 0.f;
-    int u = u0;
-    for (; u + 8 <= u1; u += 8) {
+// Sum of the unit partials [u0, u1) at one element, compensated FP32 (Neumaier).
+// A block of 256 threads handles 64 elements with 4 threads each: thread
+// group g sums the g-th quarter of the units, and the four quarters are then
+// combined in group order, so the sum has a fixed order (independent of the
+// launch) and four times the loads in flight of one thread per element.
+constexpr int RED_ELEMS = 64;
+__device__ __forceinline__ void unit_sum_quarter(const float* __restrict__ src, int64_t stride, int u0, int u1, int g,
+                                                 float& s, float& comp) {
+    const int ua = u0 + (u1 - u0) * g / 4, ub = u0 + (u1 - u0) * (g + 1) / 4;
+    s = 0.f;
+    comp = 0.f;
+    int u = ua;
+    for (; u + 8 <= ub; u += 8) {
         float q[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) q[k] = __ldg(src + (int64_t)(u + k) * stride);
 #pragma unroll
         for (int k = 0; k < 8; ++k) two_sum_acc(s, comp, q[k]);
     }
-    for (; u < u1; ++u) two_sum_acc(s, comp, __ldg(src + (int64_t)u * stride));
+    for (; u < ub; ++u) two_sum_acc(s, comp, __ldg(src + (int64_t)u * stride));
+}
+
+// Combine the four groups' (sum, compensation) pairs through shared memory;
+// returns the total in group 0's threads.
+__device__ __forceinline__ float unit_sum_combine(float s, float comp, int el, int g, float (*sh)[RED_ELEMS][2]) {
+    sh[g][el][0] = s;
+    sh[g][el][1] = comp;
+    __syncthreads();
+    float t = sh[0][el][0], c = sh[0][el][1];
+    for (int k = 1; k < 4; ++k) {
+        two_sum_acc(t, c, sh[k][el][0]);
+        c += sh[k][el][1];
+    }
+    return t + c;
+}
+
+__global__ void __launch_bounds__(256) k_adj_tc_reduce(DevData d, const int* __restrict__ cb_unit_off,
+                                                       const float* __restrict__ partial,
+                                                       const float* __restrict__ ymax,
+                                                       double* __restrict__ gsum) {
+    __shared__ float sh[4][RED_ELEMS][2];
+    const int N = d.N;
+    const int64_t NN = (int64_t)N * N;
+    const int BLK = N < 256 ? N : 256;
+    const int nbx = N / BLK;
+    const int c = blockIdx.y;
+    const int el = threadIdx.x % RED_ELEMS, g = threadIdx.x / RED_ELEMS;
+    // threads run over the partials' layout (coalesced reads); p is the pixel
+    const int64_t i = (int64_t)blockIdx.x * RED_ELEMS + el;
+    const bool in = i < NN;
+    const int blk = in ? (int)(i / ((int64_t)BLK * BLK)) : 0;
+    const int64_t loc = in ? i % ((int64_t)BLK * BLK) : 0;
+    const int cb = c * nbx * nbx + blk;
+    const int u0 = in ? cb_unit_off[cb] : 0, u1 = in ? cb_unit_off[cb + 1] : 0;
+    float s, comp;
+    unit_sum_quarter(partial + loc, (int64_t)BLK * BLK, u0, u1, g, s, comp);
+    const float tot = unit_sum_combine(s, comp, el, g, sh);
+    if (g != 0 || !in) return;
+    int nl, ml;
+    adj_partial_rc(loc, BLK, nl, ml);
+    const int64_t p = (int64_t)((blk / nbx) * BLK + nl) * N + (blk % nbx) * BLK + ml;
     const double inv = ymax ? 1.0 / (double)pow2_scale_for(ymax[0]) : 1.0;
-    gsum[(int64_t)c * NN + p] = ((double)s + (double)comp) * inv;
+    gsum[(int64_t)c * NN + p] = (double)tot * inv;
 }
 
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* cb_unit_off,
                           const float* partial, const float* ymax, double* gsum, cudaStream_t st) {
     (void)units;
-    dim3 grid(prep_blocks(d.N), d.C);
+    const int64_t NN = (int64_t)d.N * d.N;
+    dim3 grid((unsigned)((NN + RED_ELEMS - 1) / RED_ELEMS), d.C);
     k_adj_tc_reduce<<<grid, 256, 0, st>>>(d, cb_unit_off, partial, ymax, gsum);
 }
 
@@ -492,47 +521,42 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce_grad(DevData d, ImgSrc sr
                                                             const float* __restrict__ partial,
                                                             const float* __restrict__ ymax, int projected,
                                                             float* out32, double* full64, double* proj64) {
+    __shared__ float sh[4][RED_ELEMS][2];
     const int N = d.N;
     const int64_t NN = (int64_t)N * N;
     const int BLK = N < 256 ? N : 256;
     const int nbx = N / BLK;
     const int c = blockIdx.y;  // channel = image
-    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (i >= NN) return;
-    const int blk = (int)(i / ((int64_t)BLK * BLK));
-    const int64_t loc = i % ((int64_t)BLK * BLK);
+    const int el = threadIdx.x % RED_ELEMS, g = threadIdx.x / RED_ELEMS;
+    const int64_t i = (int64_t)blockIdx.x * RED_ELEMS + el;
+    const bool in = i < NN;
+    const int blk = in ? (int)(i / ((int64_t)BLK * BLK)) : 0;
+    const int64_t loc = in ? i % ((int64_t)BLK * BLK) : 0;
+    const int cb = c * nbx * nbx + blk;
+    const int u0 = in ? cb_unit_off[cb] : 0, u1 = in ? cb_unit_off[cb + 1] : 0;
+    float s, comp;
+    unit_sum_quarter(partial + loc, (int64_t)BLK * BLK, u0, u1, g, s, comp);
+    const float tot = unit_sum_combine(s, comp, el, g, sh);
+    if (g != 0 || !in) return;
     int nl, ml;
     adj_partial_rc(loc, BLK, nl, ml);
     const int64_t p = (int64_t)((blk / nbx) * BLK + nl) * N + (blk % nbx) * BLK + ml;
-    const int cb = c * nbx * nbx + blk;
-    const int u0 = cb_unit_off[cb], u1 = cb_unit_off[cb + 1];
-    const int64_t stride = (int64_t)BLK * BLK;
-    const float* srcp = partial + loc;
-    float s = 0.f, comp = 0.f;
-    int u = u0;
-    for (; u + 8 <= u1; u += 8) {
-        float q[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) q[k] = __ldg(srcp + (int64_t)(u + k) * stride);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) two_sum_acc(s, comp, q[k]);
-    }
-    for (; u < u1; ++u) two_sum_acc(s, comp, __ldg(srcp + (int64_t)u * stride));
     const double inv = ymax ? 1.0 / (double)pow2_scale_for(ymax[0]) : 1.0;
-    const double gchi = ((double)s + (double)comp) * inv;
-    double g = (double)d.beam[(int64_t)c * NN + p] * gchi;
+    const double gchi = (double)tot * inv;
+    double gr = (double)d.beam[(int64_t)c * NN + p] * gchi;
     const double x = img_value(src, c, p, NN);
-    if (d.lambda != 0.0) g += d.lambda * (1.0 + log(x / d.G));
-    const double gp = (x <= d.G && g > 0.0) ? 0.0 : g;
-    if (full64) full64[(int64_t)c * NN + p] = g;
+    if (d.lambda != 0.0) gr += d.lambda * (1.0 + log(x / d.G));
+    const double gp = (x <= d.G && gr > 0.0) ? 0.0 : gr;
+    if (full64) full64[(int64_t)c * NN + p] = gr;
     if (proj64) proj64[(int64_t)c * NN + p] = gp;
-    if (out32) out32[(int64_t)c * NN + p] = (float)(projected ? gp : g);
+    if (out32) out32[(int64_t)c * NN + p] = (float)(projected ? gp : gr);
 }
 
 void launch_adj_tc_reduce_grad(const DevData& d, const ImgSrc& src, const int* cb_unit_off, const float* partial,
                                const float* ymax, int projected, float* out32, double* full64, double* proj64,
                                cudaStream_t st) {
-    dim3 grid(prep_blocks(d.N), d.C);
+    const int64_t NN = (int64_t)d.N * d.N;
+    dim3 grid((unsigned)((NN + RED_ELEMS - 1) / RED_ELEMS), d.C);
     k_adj_tc_reduce_grad<<<grid, 256, 0, st>>>(d, src, cb_unit_off, partial, ymax, projected, out32, full64,
                                                 proj64);
 }
