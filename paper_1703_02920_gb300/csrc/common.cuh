@@ -231,6 +231,40 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
         : "memory");
 }
 
+// Whole-warp forms of the MMA issue and commit.  Every lane of the warp
+// executes them, converged, and elect.sync picks the issuing lane.  For a
+// full member mask the election is deterministic (the same lane on every
+// call), so one thread issues all of the warp's MMAs and its commits track
+// them.  A converged issue loop with an elected lane issues MMAs in fewer
+// clocks than a loop run by one lane alone.
+enum MmaCollect { MMA_PLAIN, MMA_FILL, MMA_LASTUSE };
+template <MmaCollect OP>
+__device__ __forceinline__ void umma_f16_elect(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+    if (OP == MMA_FILL)
+        asm volatile(
+            "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+    else if (OP == MMA_LASTUSE)
+        asm volatile(
+            "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+    else
+        asm volatile(
+            "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit_elect(uint64_t* bar) {
+    asm volatile(
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
 // 32 lanes x 16 consecutive 32-bit columns; thread i of the warp gets lane
 // (warp's lane quarter base + i).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {

@@ -168,7 +168,9 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
     const uint32_t tmem = S.tmem_base;
 
     if (warp == 4) {
-        if (lane == 0) {
+        // The whole warp runs the issue loop, converged (every wait's outcome is
+        // made warp-uniform), and one elected lane issues the MMAs and commits.
+        {
             const uint32_t idesc = idesc_f16kind(128, BLK, 1, 1, F16 ? 0 : 1);
             const uint32_t sbase = smem_u32(smem);
             const uint32_t lboA = (uint32_t)(R / 8) * 128, lboB = (uint32_t)(BLK / 8) * 128;
@@ -186,13 +188,13 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             for (int u = u0; u < u1 && ok; ++u) {
               const int nst = (int)((units[u].count + TCA_BK - 1) / TCA_BK);
               for (int seg0 = 0; seg0 < nst && ok; seg0 += ADJ_DRAIN, ++it) {
-                ok = mbar_wait(&S.tempty, (it & 1) ^ 1, spin, abort, status);
+                ok = __all_sync(~0u, mbar_wait(&S.tempty, (it & 1) ^ 1, spin, abort, status));
                 if (!ok) break;
                 tc_fence_after();
                 const int seg1 = min(nst, seg0 + ADJ_DRAIN);
                 for (int ks = seg0; ks < seg1; ++ks, ++sc) {
                     const int s = sc % ADJ_STAGES;
-                    ok = mbar_wait(&S.full[s], (sc / ADJ_STAGES) & 1, spin, abort, status);
+                    ok = __all_sync(~0u, mbar_wait(&S.full[s], (sc / ADJ_STAGES) & 1, spin, abort, status));
                     if (!ok) break;
                     tc_fence_after();
                     const uint64_t so = (uint64_t)((uint32_t)(s * stage_bytes) >> 4);
@@ -204,19 +206,19 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                         const uint32_t dt = tmem + (uint32_t)(mt * BLK);
                         const uint32_t acc = ks > seg0 ? 1u : 0u;
                         // products sharing an A tile read it once (collector buffer)
-                        umma_f16_collect<COLLECT_FILL>(dt, are_h, bre_h, idesc, acc);
-                        umma_f16_collect<COLLECT_LASTUSE>(dt, are_h, bre_l, idesc, 1u);
-                        umma_bf16(dt, are_l, bre_h, idesc, 1u);
-                        umma_f16_collect<COLLECT_FILL>(dt, aim_h, bim_h, idesc, 1u);
-                        umma_f16_collect<COLLECT_LASTUSE>(dt, aim_h, bim_l, idesc, 1u);
-                        umma_bf16(dt, aim_l, bim_h, idesc, 1u);
+                        umma_f16_elect<MMA_FILL>(dt, are_h, bre_h, idesc, acc);
+                        umma_f16_elect<MMA_LASTUSE>(dt, are_h, bre_l, idesc, 1u);
+                        umma_f16_elect<MMA_PLAIN>(dt, are_l, bre_h, idesc, 1u);
+                        umma_f16_elect<MMA_FILL>(dt, aim_h, bim_h, idesc, 1u);
+                        umma_f16_elect<MMA_LASTUSE>(dt, aim_h, bim_l, idesc, 1u);
+                        umma_f16_elect<MMA_PLAIN>(dt, aim_l, bim_h, idesc, 1u);
                     }
-                    umma_commit(&S.empty[s]);
+                    umma_commit_elect(&S.empty[s]);
                 }
-                if (ok) umma_commit(&S.tfull);
+                if (ok) umma_commit_elect(&S.tfull);
               }
             }
-            umma_commit(&S.drain);
+            umma_commit_elect(&S.drain);
             int dummy = 0;
             mbar_wait(&S.drain, 0, drain_limit(spin), (volatile int*)&dummy, status);
         }
