@@ -203,26 +203,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
-// The same MMA keeping its A tile in the tensor core's collector buffer for
-// the next MMA of this thread (FILL), or taking A from that buffer and
-// releasing it (LASTUSE): two consecutive products with the same A tile read
-// it from shared memory once.
-enum CollectorA { COLLECT_FILL, COLLECT_LASTUSE };
-template <CollectorA OP>
-__device__ __forceinline__ void umma_f16_collect(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                                 uint32_t accumulate) {
-    if (OP == COLLECT_FILL)
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-    else
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-
 // Arrive on an mbarrier once all previously issued tcgen05 ops of this thread complete.
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile(
@@ -236,7 +216,10 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 // full member mask the election is deterministic (the same lane on every
 // call), so one thread issues all of the warp's MMAs and its commits track
 // them.  A converged issue loop with an elected lane issues MMAs in fewer
-// clocks than a loop run by one lane alone.
+// clocks than a loop run by one lane alone.  MMA_FILL keeps the MMA's A tile
+// in the tensor core's collector buffer for the issuing thread's next MMA,
+// MMA_LASTUSE takes A from that buffer and releases it: two consecutive
+// products with the same A tile read it from shared memory once.
 enum MmaCollect { MMA_PLAIN, MMA_FILL, MMA_LASTUSE };
 template <MmaCollect OP>
 __device__ __forceinline__ void umma_f16_elect(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -263,6 +246,33 @@ __device__ __forceinline__ void umma_commit_elect(uint64_t* bar) {
         " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
             smem_u32(bar))
         : "memory");
+}
+
+
+// The six MMAs of one streaming-forward stage (two K steps, each hi x hi,
+// hi x lo, lo x hi; the first two share their A tile through the collector
+// buffer) in one block, whole-warp form (elect.sync picks the issuing lane, as
+// in umma_f16_elect).  Each descriptor is assembled from its low word (start
+// address field already moved to the stage's slot; ka / kb move it to the
+// second K step) and the high word it shares with its operand's other planes.
+// acc = 0 starts a fresh accumulation with the first MMA.
+__device__ __forceinline__ void umma6_stage_elect(uint32_t dt, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
+                                                  uint32_t hia, uint32_t hib, uint32_t ka, uint32_t kb,
+                                                  uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p, one, e;\n .reg .b64 d0, d1, d2, d3, d4, d5, d6, d7;\n .reg .b32 t0, t1, t2, t3;\n"
+        " setp.ne.b32 p, %10, 0;\n setp.ne.b32 one, %11, 0;\n"
+        " elect.sync _|e, 0xffffffff;\n"
+        " mov.b64 d0, {%1, %5};\n mov.b64 d1, {%2, %5};\n mov.b64 d2, {%3, %6};\n mov.b64 d3, {%4, %6};\n"
+        " add.u32 t0, %1, %7;\n add.u32 t1, %2, %7;\n add.u32 t2, %3, %8;\n add.u32 t3, %4, %8;\n"
+        " mov.b64 d4, {t0, %5};\n mov.b64 d5, {t1, %5};\n mov.b64 d6, {t2, %6};\n mov.b64 d7, {t3, %6};\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], d0, d2, %9, p;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], d0, d3, %9, one;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], d1, d2, %9, one;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], d4, d6, %9, one;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], d4, d7, %9, one;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], d5, d6, %9, one;\n}\n" ::"r"(dt),
+        "r"(ah), "r"(al), "r"(bh), "r"(bl), "r"(hia), "r"(hib), "r"(ka), "r"(kb), "r"(idesc), "r"(acc), "r"(1u));
 }
 
 // 32 lanes x 16 consecutive 32-bit columns; thread i of the warp gets lane

@@ -30,7 +30,7 @@
 // stays at the level of a 256-row image whatever N is.
 //
 // Roles (448 threads): warps 0-3 epilogue (TMEM lane = A row), warp 4 MMA
-// issuer + TMEM owner, warp 5 bulk copies of the image operand chunks,
+// issue (one elected lane) + TMEM owner, warp 5 bulk copies of the image operand chunks,
 // warps 6-13 Ey producers.  Every mbarrier wait is bounded.
 #include <cstdint>
 
@@ -117,54 +117,54 @@ __global__ void __launch_bounds__(F2_THREADS, 1)
 
     if (warp == 4) {
         // ---------------------------------------------------------------- MMA
-        if (lane == 0) {
+        // The whole warp runs the issue loop, converged (every wait's outcome
+        // is made warp-uniform), and one elected lane issues the MMAs and
+        // commits.
+        {
             const uint32_t idesc = idesc_f16kind(128, BN, 0, 0, F16 ? 0 : 1);
             const uint32_t sbase = smem_u32(smem);
             const uint32_t lboB = (uint32_t)(BN / 8) * 128;
             // Operand descriptors of slot 0; another slot or K step only moves
-            // the start address, whose field (address >> 4, low 14 bits) takes
-            // the offset by plain addition (shared memory < 256 KB, no carry).
+            // the start address, whose field (address >> 4, low 14 bits of the
+            // low word) takes the offset by plain 32-bit addition (shared
+            // memory < 256 KB, no carry).  A second K step is 2 core-matrix
+            // columns on: 2 x 2048 bytes in A, 2 x lboB in B.
             const uint64_t d_ah = smem_desc(sbase, 2048, 128);
             const uint64_t d_al = smem_desc(sbase + F2_APLANE, 2048, 128);
             const uint64_t d_bh = smem_desc(sbase + F2_ABYTES, lboB, 128);
             const uint64_t d_bl = smem_desc(sbase + F2_ABYTES + BN * TC_BK * 2, lboB, 128);
+            const uint32_t lo_ah = (uint32_t)d_ah, lo_al = (uint32_t)d_al;
+            const uint32_t lo_bh = (uint32_t)d_bh, lo_bl = (uint32_t)d_bl;
+            const uint32_t hi_a = (uint32_t)(d_ah >> 32), hi_b = (uint32_t)(d_bh >> 32);
+            const uint32_t ka16 = (2u * 2048u) >> 4, kb16 = (2u * lboB) >> 4;
+            static_assert(TC_BK == 32, "one stage is two K steps of 16");
             uint32_t sc = 0, it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 for (int u = 0; u < n_mb * n_seg && ok; ++u, ++it) {
                     const int b = it & 1;
                     const int ks0 = (u % n_seg) * kseg;  // first stage of this accumulation
-                    ok = mbar_wait(&S.tempty[b], ((it >> 1) & 1) ^ 1, spin, abort, status);
+                    ok = __all_sync(~0u, mbar_wait(&S.tempty[b], ((it >> 1) & 1) ^ 1, spin, abort, status));
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t dt = tmem + (uint32_t)(b * BN);
                     for (int ks = ks0; ks < ks0 + kseg; ++ks, ++sc) {
                         const int s = sc % F2_STAGES;
                         // one wait: the producers' tables and the image chunk
-                        ok = mbar_wait(&S.full[s], (sc / F2_STAGES) & 1, spin, abort, status);
+                        ok = __all_sync(~0u, mbar_wait(&S.full[s], (sc / F2_STAGES) & 1, spin, abort, status));
                         if (!ok) break;
                         tc_fence_after();
-                        const uint64_t so = (uint64_t)((uint32_t)(s * stage_bytes) >> 4);
-#pragma unroll
-                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                            const uint64_t ao = so + (uint64_t)(kk * 2 * 2048 >> 4);
-                            const uint64_t bo = so + (uint64_t)(kk * 2 * lboB >> 4);
-                            const uint64_t a_h = d_ah + ao, a_l = d_al + ao;
-                            const uint64_t b_h = d_bh + bo, b_l = d_bl + bo;
-                            const uint32_t acc = (ks > ks0 || kk > 0) ? 1u : 0u;
-                            // hi x hi and hi x lo share the A tile: one read
-                            umma_f16_collect<COLLECT_FILL>(dt, a_h, b_h, idesc, acc);
-                            umma_f16_collect<COLLECT_LASTUSE>(dt, a_h, b_l, idesc, 1u);
-                            umma_bf16(dt, a_l, b_h, idesc, 1u);
-                        }
-                        umma_commit(&S.empty[s]);
+                        const uint32_t so = (uint32_t)(s * stage_bytes) >> 4;
+                        umma6_stage_elect(dt, lo_ah + so, lo_al + so, lo_bh + so, lo_bl + so, hi_a, hi_b, ka16,
+                                          kb16, idesc, ks > ks0 ? 1u : 0u);
+                        umma_commit_elect(&S.empty[s]);
                     }
-                    if (ok) umma_commit(&S.tfull[b]);
+                    if (ok) umma_commit_elect(&S.tfull[b]);
                 }
             }
             // every issued MMA completes before TMEM is released (its operands
             // were complete when it was issued)
-            umma_commit(&S.drain);
+            umma_commit_elect(&S.drain);
             int dummy = 0;
             mbar_wait(&S.drain, 0, drain_limit(spin), (volatile int*)&dummy, status);
         }
