@@ -77,9 +77,10 @@ struct mem_ctx {
     double* bf64 = nullptr;
     uint16_t* planes = nullptr;
     float* cmean = nullptr;  // column means of the centred tensor-core operand
-    float *cmax = nullptr, *cscale = nullptr;   // FP16X3 operand scales per channel
+    float* cscale = nullptr;                    // FP16X3 operand scales per channel
     double* col_psum = nullptr;                 // column-mean partial sums
     float* col_pmax = nullptr;
+    unsigned* col_count = nullptr;              // column-mean completion counters (zero between calls)
     float *ymax = nullptr, *ymax_part = nullptr;  // FP16X3: max |y| (adjoint operand scale), partials
     float* partial = nullptr;  // adjoint unit partials (FP32, one BLK x BLK block each)
     int* dstatus = nullptr;
@@ -374,7 +375,10 @@ mem_status ensure_buffers(mem_ctx* c) {
     } else {
         TRY(dalloc(c, &c->planes, (size_t)2 * c->C * NN));
         TRY(dalloc(c, &c->cmean, (size_t)c->C * c->N));
-        TRY(dalloc(c, &c->cmax, (size_t)c->C * colmean_blocks(c->N)));
+        if (!c->col_count) {
+            TRY(dalloc(c, &c->col_count, (size_t)c->C));
+            CK(cudaMemsetAsync(c->col_count, 0, (size_t)c->C * sizeof(unsigned), c->st), "column-mean counters");
+        }
         TRY(dalloc(c, &c->col_psum, (size_t)colmean_tmp_count(c->N, c->C)));
         TRY(dalloc(c, &c->col_pmax, (size_t)colmean_tmp_count(c->N, c->C)));
         TRY(dalloc(c, &c->cscale, (size_t)c->C));
@@ -407,26 +411,28 @@ void* bbuf(mem_ctx* c) {
            : c->prec == MEM_PREC_FP32_DIRECT ? (void*)c->bf32 : (void*)c->planes;
 }
 
-// prep + forward for one image source.  mode: FwdMode.
-mem_status run_forward(mem_ctx* c, const ImgSrc& src, int mode, bool entropy, void* yout) {
+// prep + forward for one image source.  mode: FwdMode.  defer_scalars: the
+// objective's scalar reduction is left to a later launch (the gradient's).
+mem_status run_forward(mem_ctx* c, const ImgSrc& src, int mode, bool entropy, void* yout,
+                       bool defer_scalars = false) {
     DevData d = c->dd();
     const bool tc = is_tc(c->prec);
     const int f16 = c->prec == MEM_PREC_FP16X3;
+    // FP16X3: the weighted residual's maximum for the adjoint's operand scale
+    // (zeroed by the column-mean kernel)
+    float* ymax = (tc && f16 && mode == FWD_RESID) ? c->ymax : nullptr;
     if (tc) {
         KTimer t(c, "colmean");
-        launch_colmean(d, src, c->cmean, c->cmax, c->col_psum, c->col_pmax, c->st);
-        c->launches += 2;
+        launch_colmean(d, src, c->cmean, c->cscale, c->col_psum, c->col_pmax, c->col_count, ymax, c->st);
+        c->launches++;
     }
     {
         KTimer t(c, "prep");
         launch_prep(d, src, bformat(c->prec), bbuf(c), entropy ? c->ent_part : nullptr, tc ? c->cmean : nullptr,
-                    c->cmax, c->cscale, c->st);
+                    c->cscale, c->st);
     }
     c->launches++;
     TRY(after_launch(c, "prep kernel"));
-    // FP16X3: the weighted residual's maximum for the adjoint's operand scale
-    float* ymax = (tc && f16 && mode == FWD_RESID) ? c->ymax : nullptr;
-    if (ymax) CK(cudaMemsetAsync(ymax, 0, sizeof(float), c->st), "residual maximum");
     if (tc && c->fwd_kernel == MEM_FWD_RESIDENT) {
         KTimer t(c, "fwd_rs");
         launch_fwd_rs(d, f16, c->tiles_tc, c->n_tiles_tc, c->planes, c->cmean, c->cscale, mode, (float2*)yout,
@@ -443,7 +449,7 @@ mem_status run_forward(mem_ctx* c, const ImgSrc& src, int mode, bool entropy, vo
     }
     if ((tc ? c->n_tiles_tc : c->n_tiles) > 0) c->launches++;
     TRY(after_launch(c, "forward kernel"));
-    if (mode != FWD_VIS) {
+    if (mode != FWD_VIS && !defer_scalars) {
         KTimer t(c, "scalars");
         launch_scalars(d, tc ? c->tile_off_tc : c->tile_off, c->chi_part, c->ent_part, entropy ? 1 : 0,
                        c->scal, c->img_tmp, c->st);
@@ -496,16 +502,23 @@ mem_status run_objgrad(mem_ctx* c, const ImgSrc& src, int projected, float* out3
                        double* proj64) {
     TRY(ensure_buffers(c));
     void* yout = c->prec == MEM_PREC_FP64_DIRECT ? (void*)c->y64 : (void*)c->y32;
-    TRY(run_forward(c, src, FWD_RESID, true, yout));
-    int ks = 1;
-    // images of one channel each: the adjoint's unit-partial sum and the
-    // gradient assembly are one launch
+    // images of one channel each: the adjoint's unit-partial sum, the
+    // gradient assembly and the objective's scalar reduction are one launch
     const bool fused = is_tc(c->prec) && !c->shared;
+    TRY(run_forward(c, src, FWD_RESID, true, yout, fused));
+    int ks = 1;
     TRY(run_adjoint(c, &ks, true, !fused));
     if (fused) {
         KTimer t(c, "adj_reduce_grad");
+        ScalarArgs sc;
+        sc.tile_off = c->tile_off_tc;
+        sc.chi_part = c->chi_part;
+        sc.ent_part = c->ent_part;
+        sc.with_entropy = 1;
+        sc.scal = c->scal;
+        sc.img_tmp = c->img_tmp;
         launch_adj_tc_reduce_grad(c->dd(), src, c->cb_off, c->partial, c->prec == MEM_PREC_FP16X3 ? c->ymax : nullptr,
-                                  projected, out32, full64, proj64, c->st);
+                                  projected, out32, full64, proj64, sc, c->st);
     } else {
         KTimer t(c, "finalize");
         launch_finalize(c->dd(), src, c->gsum, ks, projected, out32, full64, proj64, c->st);

@@ -89,21 +89,23 @@ void launch_phase_prep(int64_t Z, const double* u, const double* v, double dx, d
 // B_c = A_c * img(c) for every channel in the requested format; entropy
 // partials S_i per (image, block) when ent_part != nullptr.  The tensor-core
 // formats hold B - c_m (c_m the column mean from launch_colmean); F16X3 also
-// scales each channel by cscale[c] (a power of two, written here).
+// scales each channel by cscale[c] (a power of two, from launch_colmean).
 void launch_prep(const DevData& d, const ImgSrc& src, int fmt, void* bout, double* ent_part,
-                 const float* cmean, const float* cmax, float* cscale, cudaStream_t st);
-// Column means of B_c per channel into cmean[C][N]; per 32-column block the
-// bound max|B| + |c_m| into cmax[C][ceil(N/32)].
-// psum (double) and pmax (float) hold colmean_tmp_count(N, C) entries each.
-void launch_colmean(const DevData& d, const ImgSrc& src, float* cmean, float* cmax, double* psum,
-                    float* pmax, cudaStream_t st);
+                 const float* cmean, const float* cscale, cudaStream_t st);
+// Column means of B_c per channel into cmean[C][N] and the channel's FP16X3
+// operand scale into cscale[C] (from the bound max_m (max_n |B| + |c_m|)).
+// psum (double) and pmax (float) hold colmean_tmp_count(N, C) entries each;
+// count holds C completion counters, zero between calls (each call leaves
+// them zero).  ymax_clear (nullable) is set to zero.
+void launch_colmean(const DevData& d, const ImgSrc& src, float* cmean, float* cscale, double* psum, float* pmax,
+                    unsigned* count, float* ymax_clear, cudaStream_t st);
 int colmean_tmp_count(int N, int C);
 __host__ __device__ inline int colmean_blocks(int N) { return (N + 31) / 32; }
 // max |component| of n floats into ymax[0]; the FP16X3 adjoint scales y by
 // pow2_scale_for(ymax[0]).  The forward writes the same maximum of the y it
 // produces (RESID mode) when given ymax (zeroed before).
 void launch_absmax(int64_t n, const float* y, float* part, float* ymax, cudaStream_t st);
-int prep_blocks(int N);
+__host__ __device__ inline int prep_blocks(int N) { return (int)(((int64_t)N * N + 255) / 256); }
 
 void launch_fwd_direct(const DevData& d, int fp64, const VisTile* tiles, int n_tiles, const void* B,
                        int mode, void* yout, double* chi_part, cudaStream_t st);
@@ -163,11 +165,22 @@ void launch_adj_tc_reduce_out(int N, const int* cb_unit_off, const float* partia
 // ymax (nullable, FP16X3): partials are divided by pow2_scale_for(ymax[0]).
 void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* unit_off_by_chan_blk,
                           const float* partial, const float* ymax, double* gsum, cudaStream_t st);
+// Inputs of the objective's scalar reduction (launch_scalars) when it runs
+// inside another launch; scal == nullptr: not run.
+struct ScalarArgs {
+    const int* tile_off = nullptr;
+    const double* chi_part = nullptr;
+    const double* ent_part = nullptr;
+    int with_entropy = 0;
+    double* scal = nullptr;
+    double* img_tmp = nullptr;
+};
 // Unit-partial sum plus gradient assembly in one launch, for images of one
-// channel each (not the shared-image mode).
+// channel each (not the shared-image mode); with sc.scal set, the same launch
+// also forms the objective scalars (as launch_scalars).
 void launch_adj_tc_reduce_grad(const DevData& d, const ImgSrc& src, const int* cb_unit_off, const float* partial,
                                const float* ymax, int projected, float* out32, double* full64, double* proj64,
-                               cudaStream_t st);
+                               const ScalarArgs& sc, cudaStream_t st);
 
 // grad_i = sum_{c in image i} A_c * sum_k gsum[k][c] + lambda (1 + log(I/G)); optional projection.
 void launch_finalize(const DevData& d, const ImgSrc& src, const double* gsum, int ks, int projected,

@@ -8,6 +8,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "reduce.cuh"
 
 namespace msk {
 
@@ -31,23 +32,6 @@ void launch_phase_prep(int64_t Z, const double* u, const double* v, double dx, d
     k_phase_prep<<<(unsigned)((Z + 255) / 256), 256, 0, st>>>(Z, u, v, dx, dy, pa, pb);
 }
 
-// ---------------------------------------------------------------------------
-// block reductions (fixed tree: deterministic)
-// ---------------------------------------------------------------------------
-template <int BLOCK>
-__device__ __forceinline__ double block_sum(double x, double* sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = x;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < BLOCK / 32; ++i) r += sh[i];
-    }
-    __syncthreads();
-    return r;  // valid in thread 0
-}
 
 template <int BLOCK>
 __device__ __forceinline__ double block_max(double x, double* sh) {
@@ -86,19 +70,29 @@ __device__ __forceinline__ int64_t tc_plane_index(int n, int m, int N, int BN) {
 // Column means c_m = (1/N) sum_n B[n][m] per channel (the operand of the
 // tensor-core forward is centred column by column, see k_fwd_tc), in two
 // stages with a fixed summation order.  Stage 1: block (column block of 32,
-// row block rb of N/COL_RB rows) -> partial sums and max |B| per column.
+// row block rb of N/COL_RB rows, channel) -> partial sums and max |B| per
+// column.  Stage 2, run by the channel's last stage-1 block to finish (a
+// completion counter per channel, which that block resets): c_m, then the
+// bound max_n |B[n][m] - c_m| <= max|B| + |c_m| maximised over the channel,
+// and from it the channel's power-of-two FP16X3 operand scale.
 constexpr int COL_RB = 16;
 
-__global__ void __launch_bounds__(256) k_colsum_part(DevData d, ImgSrc src, double* __restrict__ psum,
-                                                     float* __restrict__ pmax) {
+__global__ void __launch_bounds__(256) k_colsum(DevData d, ImgSrc src, double* __restrict__ psum,
+                                                float* __restrict__ pmax, unsigned* __restrict__ count,
+                                                float* __restrict__ cmean, float* __restrict__ cscale,
+                                                float* __restrict__ ymax_clear) {
     __shared__ double sh[8][33];
     __shared__ float shm[8][33];
+    __shared__ bool last;
     const int N = d.N;
     const int64_t NN = (int64_t)N * N;
     const int c = blockIdx.z, rb = blockIdx.y;
     const int i = image_of(d, c);
-    const int m = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int lane = threadIdx.x & 31;
+    const int m = blockIdx.x * 32 + lane;
     const int rg = threadIdx.x >> 5;
+    // the FP16X3 residual maximum of the forward that follows starts at zero
+    if (ymax_clear && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) *ymax_clear = 0.f;
     const int n0 = (int)((int64_t)N * rb / COL_RB), n1 = (int)((int64_t)N * (rb + 1) / COL_RB);
     double acc = 0.0;
     float amax = 0.f;
@@ -112,61 +106,59 @@ __global__ void __launch_bounds__(256) k_colsum_part(DevData d, ImgSrc src, doub
             amax = fmaxf(amax, (float)fabs(b));
         }
     }
-    sh[rg][threadIdx.x & 31] = acc;
-    shm[rg][threadIdx.x & 31] = amax;
+    sh[rg][lane] = acc;
+    shm[rg][lane] = amax;
     __syncthreads();
     if (rg == 0 && m < N) {
         double t = 0.0;
         float mx = 0.f;
         for (int k = 0; k < 8; ++k) {
-            t += sh[k][threadIdx.x];
-            mx = fmaxf(mx, shm[k][threadIdx.x]);
+            t += sh[k][lane];
+            mx = fmaxf(mx, shm[k][lane]);
         }
         psum[((int64_t)c * COL_RB + rb) * N + m] = t;
         pmax[((int64_t)c * COL_RB + rb) * N + m] = mx;
     }
-}
-
-// Stage 2: one block per channel: c_m, and per 32-column block the bound
-// max_n |B[n][m] - c_m| <= max |B| + |c_m| into cmax[C][ceil(N/32)].
-__global__ void __launch_bounds__(256) k_colsum_final(int N, const double* __restrict__ psum,
-                                                      const float* __restrict__ pmax,
-                                                      float* __restrict__ cmean, float* __restrict__ cmax) {
-    const int c = blockIdx.x;
-    for (int mb = threadIdx.x >> 5; mb < colmean_blocks(N); mb += 8) {
-        const int m = mb * 32 + (threadIdx.x & 31);
-        float bound = 0.f;
-        if (m < N) {
-            double t = 0.0;
-            float mx = 0.f;
-            for (int rb = 0; rb < COL_RB; ++rb) {
-                t += psum[((int64_t)c * COL_RB + rb) * N + m];
-                mx = fmaxf(mx, pmax[((int64_t)c * COL_RB + rb) * N + m]);
-            }
-            const float cm = (float)(t / N);
-            cmean[(int64_t)c * N + m] = cm;
-            bound = mx + fabsf(cm);
-        }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&count[c], 1u) == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // stage 2: the partials of channel c in row-block order (read through L2)
+    float bound = 0.f;
+    for (int mm = threadIdx.x; mm < N; mm += blockDim.x) {
+        double t = 0.0;
+        float mx = 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) bound = fmaxf(bound, __shfl_down_sync(0xffffffffu, bound, o));
-        if ((threadIdx.x & 31) == 0) cmax[(int64_t)c * colmean_blocks(N) + mb] = bound;
+        for (int r = 0; r < COL_RB; ++r) {
+            t += __ldcg(psum + ((int64_t)c * COL_RB + r) * N + mm);
+            mx = fmaxf(mx, __ldcg(pmax + ((int64_t)c * COL_RB + r) * N + mm));
+        }
+        const float cm = (float)(t / N);
+        cmean[(int64_t)c * N + mm] = cm;
+        bound = fmaxf(bound, mx + fabsf(cm));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bound = fmaxf(bound, __shfl_down_sync(0xffffffffu, bound, o));
+    if (lane == 0) shm[0][rg] = bound;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float mx = 0.f;
+        for (int k = 0; k < 8; ++k) mx = fmaxf(mx, shm[0][k]);
+        cscale[c] = pow2_scale_for(mx);
+        count[c] = 0;  // ready for the next evaluation
     }
 }
 
-void launch_colmean(const DevData& d, const ImgSrc& src, float* cmean, float* cmax, double* psum,
-                    float* pmax, cudaStream_t st) {
-    k_colsum_part<<<dim3(colmean_blocks(d.N), COL_RB, d.C), 256, 0, st>>>(d, src, psum, pmax);
-    k_colsum_final<<<d.C, 256, 0, st>>>(d.N, psum, pmax, cmean, cmax);
+void launch_colmean(const DevData& d, const ImgSrc& src, float* cmean, float* cscale, double* psum, float* pmax,
+                    unsigned* count, float* ymax_clear, cudaStream_t st) {
+    k_colsum<<<dim3(colmean_blocks(d.N), COL_RB, d.C), 256, 0, st>>>(d, src, psum, pmax, count, cmean, cscale,
+                                                                    ymax_clear);
 }
 
 int colmean_tmp_count(int N, int C) { return COL_RB * N * C; }
-
-// Power-of-two scale of channel c from its column-block bounds.
-__device__ __forceinline__ float chan_scale(const float* cmax, int c, int nb) {
-    float mx = 0.f;
-    for (int k = 0; k < nb; ++k) mx = fmaxf(mx, cmax[(int64_t)c * nb + k]);
-    return pow2_scale_for(mx);
-}
 
 // max |y| over n floats: 256 block maxima, then one block forms the scale.
 __global__ void __launch_bounds__(256) k_absmax_part(int64_t n, const float* __restrict__ y,
@@ -200,7 +192,7 @@ void launch_absmax(int64_t n, const float* y, float* part, float* ymax, cudaStre
 
 __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, void* bout,
                                               double* ent_part, const float* __restrict__ cmean,
-                                              const float* __restrict__ cmax, float* cscale) {
+                                              const float* __restrict__ cscale) {
     __shared__ double sh[8];
     const int N = d.N;
     const int64_t NN = (int64_t)N * N;
@@ -242,8 +234,7 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
                 base[q] = hi;
                 base[q + (int64_t)BN * TC_BK] = lo;
             } else {
-                const float sc = chan_scale(cmax, c, colmean_blocks(N));
-                if (p == 0) cscale[c] = sc;
+                const float sc = cscale[c];
                 const float bf = (float)(cb * (double)sc);
                 __half hi = __float2half_rn(bf);
                 __half lo = __float2half_rn(bf - __half2float(hi));
@@ -259,12 +250,11 @@ __global__ void __launch_bounds__(256) k_prep(DevData d, ImgSrc src, int fmt, vo
     }
 }
 
-int prep_blocks(int N) { return (int)(((int64_t)N * N + 255) / 256); }
 
 void launch_prep(const DevData& d, const ImgSrc& src, int fmt, void* bout, double* ent_part,
-                 const float* cmean, const float* cmax, float* cscale, cudaStream_t st) {
+                 const float* cmean, const float* cscale, cudaStream_t st) {
     dim3 grid(prep_blocks(d.N), d.C);
-    k_prep<<<grid, 256, 0, st>>>(d, src, fmt, bout, ent_part, cmean, cmax, cscale);
+    k_prep<<<grid, 256, 0, st>>>(d, src, fmt, bout, ent_part, cmean, cscale);
 }
 
 // ---------------------------------------------------------------------------
@@ -478,80 +468,20 @@ void launch_finalize(const DevData& d, const ImgSrc& src, const double* gsum, in
 // Ordered FP64 reductions of tile partials into per-image and total scalars.
 // scal layout: [0..2] = Phi, chi^2, S totals; [3 + 3i ...] per image.
 // ---------------------------------------------------------------------------
-// Grid (images, SCAL_SPLIT); block (i, q) sums a contiguous share of image
-// i's chi^2 partials and entropy partials in a fixed order; the last block to
-// finish adds the shares in order.
-constexpr int SCAL_SPLIT = 32;
-
 __global__ void __launch_bounds__(256) k_scalars(DevData d, const int* __restrict__ tile_off,
                                                  const double* __restrict__ chi_part,
                                                  const double* __restrict__ ent_part, int with_entropy,
                                                  int n_ent_blocks, double* part, double* img_tmp, double* scal,
                                                  unsigned* counter) {
-    __shared__ double sh[8];
-    __shared__ bool last;
-    const int i = blockIdx.x, q = blockIdx.y;
-    int c_lo = d.shared ? 0 : i, c_hi = d.shared ? d.C : i + 1;
-    const int64_t t0 = 4LL * tile_off[c_lo], t1 = 4LL * tile_off[c_hi];  // channels are contiguous
-    const int64_t len = t1 - t0;
-    const int64_t a = t0 + len * q / SCAL_SPLIT, b = t0 + len * (q + 1) / SCAL_SPLIT;
-    double x = 0.0;
-    for (int64_t t = a + threadIdx.x; t < b; t += 256) x += chi_part[t];
-    const double chi = block_sum<256>(x, sh);
-    double S = 0.0;
-    if (with_entropy) {
-        const int e0 = (int)((int64_t)n_ent_blocks * q / SCAL_SPLIT), e1 = (int)((int64_t)n_ent_blocks * (q + 1) / SCAL_SPLIT);
-        double y = 0.0;
-        for (int e = e0 + threadIdx.x; e < e1; e += 256) y += ent_part[(int64_t)i * n_ent_blocks + e];
-        S = block_sum<256>(y, sh);
-    }
-    if (threadIdx.x == 0) {
-        part[((int64_t)i * SCAL_SPLIT + q) * 2] = chi;
-        part[((int64_t)i * SCAL_SPLIT + q) * 2 + 1] = S;
-        // the last block to finish forms the totals
-        __threadfence();
-        last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // Stage 2 (last block): one thread per image sums its SCAL_SPLIT partials
-    // in order (read through L2); thread 0 then forms the totals in image order
-    for (int im = threadIdx.x; im < d.n_images; im += blockDim.x) {
-        double c2 = 0.0, s2 = 0.0;
-        for (int k = 0; k < SCAL_SPLIT; ++k) {
-            c2 += __ldcg(part + ((int64_t)im * SCAL_SPLIT + k) * 2);
-            s2 += __ldcg(part + ((int64_t)im * SCAL_SPLIT + k) * 2 + 1);
-        }
-        img_tmp[3 * im] = c2 - d.lambda * s2;
-        img_tmp[3 * im + 1] = c2;
-        img_tmp[3 * im + 2] = s2;
-        scal[3 + 3 * im] = c2 - d.lambda * s2;
-        scal[4 + 3 * im] = c2;
-        scal[5 + 3 * im] = s2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double ta = 0, tb = 0, tc = 0;
-        for (int im = 0; im < d.n_images; ++im) {
-            ta += img_tmp[3 * im];
-            tb += img_tmp[3 * im + 1];
-            tc += img_tmp[3 * im + 2];
-        }
-        scal[0] = ta;
-        scal[1] = tb;
-        scal[2] = tc;
-        *counter = 0;  // ready for the next evaluation
-    }
+    scalars_block(d, tile_off, chi_part, ent_part, with_entropy, n_ent_blocks, part, img_tmp, scal, counter,
+                  blockIdx.x, blockIdx.y);
 }
 
 void launch_scalars(const DevData& d, const int* tile_off, const double* chi_part,
                     const double* ent_part, int with_entropy, double* scal, double* img_tmp,
                     cudaStream_t st) {
-    // img_tmp: 3 * n_images totals, 2 * SCAL_SPLIT * n_images partials, then the
-    // completion counter (zero between evaluations)
-    double* part = img_tmp + 3 * d.n_images;
-    unsigned* counter = (unsigned*)(part + 2 * SCAL_SPLIT * d.n_images);
+    double* part = scalars_part(img_tmp, d.n_images);
+    unsigned* counter = scalars_counter(img_tmp, d.n_images);
     k_scalars<<<dim3(d.n_images, SCAL_SPLIT), 256, 0, st>>>(d, tile_off, chi_part, ent_part, with_entropy,
                                                              prep_blocks(d.N), part, img_tmp, scal, counter);
 }

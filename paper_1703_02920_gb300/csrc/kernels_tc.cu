@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "reduce.cuh"
 
 namespace msk {
 
@@ -518,19 +519,32 @@ void launch_adj_tc_reduce(const DevData& d, const AdjUnit* units, const int* cb_
 // log(I/G) stays FP64: with an FP32 log the 50-iteration solve of the
 // 64x64 problem ended 1.4e-3 (relative L2) from the oracle's image in the
 // BF16X3 form, against 4.6e-4.
+// With sc.scal set, SCAL_SPLIT further blocks per image (the first ones in
+// x, so that they start with the first wave) run the objective's scalar
+// reduction (scalars_block): it needs only the forward's chi^2 partials and
+// the prep's entropy partials, so it shares this launch instead of taking one
+// of its own.
 __global__ void __launch_bounds__(256) k_adj_tc_reduce_grad(DevData d, ImgSrc src,
                                                             const int* __restrict__ cb_unit_off,
                                                             const float* __restrict__ partial,
                                                             const float* __restrict__ ymax, int projected,
-                                                            float* out32, double* full64, double* proj64) {
+                                                            float* out32, double* full64, double* proj64,
+                                                            ScalarArgs sc) {
     __shared__ float sh[4][RED_ELEMS][2];
     const int N = d.N;
     const int64_t NN = (int64_t)N * N;
+    const int n_scal = sc.scal ? SCAL_SPLIT : 0;
+    if ((int)blockIdx.x < n_scal) {
+        scalars_block(d, sc.tile_off, sc.chi_part, sc.ent_part, sc.with_entropy, prep_blocks(N),
+                      scalars_part(sc.img_tmp, d.n_images), sc.img_tmp, sc.scal,
+                      scalars_counter(sc.img_tmp, d.n_images), blockIdx.y, blockIdx.x);
+        return;
+    }
     const int BLK = N < 256 ? N : 256;
     const int nbx = N / BLK;
     const int c = blockIdx.y;  // channel = image
     const int el = threadIdx.x % RED_ELEMS, g = threadIdx.x / RED_ELEMS;
-    const int64_t i = (int64_t)blockIdx.x * RED_ELEMS + el;
+    const int64_t i = (int64_t)(blockIdx.x - n_scal) * RED_ELEMS + el;
     const bool in = i < NN;
     const int blk = in ? (int)(i / ((int64_t)BLK * BLK)) : 0;
     const int64_t loc = in ? i % ((int64_t)BLK * BLK) : 0;
@@ -556,11 +570,12 @@ __global__ void __launch_bounds__(256) k_adj_tc_reduce_grad(DevData d, ImgSrc sr
 
 void launch_adj_tc_reduce_grad(const DevData& d, const ImgSrc& src, const int* cb_unit_off, const float* partial,
                                const float* ymax, int projected, float* out32, double* full64, double* proj64,
-                               cudaStream_t st) {
+                               const ScalarArgs& sc, cudaStream_t st) {
     const int64_t NN = (int64_t)d.N * d.N;
-    dim3 grid((unsigned)((NN + RED_ELEMS - 1) / RED_ELEMS), d.C);
+    const unsigned gb = (unsigned)((NN + RED_ELEMS - 1) / RED_ELEMS);
+    dim3 grid(gb + (sc.scal ? SCAL_SPLIT : 0), d.C);
     k_adj_tc_reduce_grad<<<grid, 256, 0, st>>>(d, src, cb_unit_off, partial, ymax, projected, out32, full64,
-                                                proj64);
+                                                proj64, sc);
 }
 
 }  // namespace msk
