@@ -589,8 +589,10 @@ def main():
                            "precision": args.precision,
                            "image": f"{N}x{N}", "visibilities": Z, "parallelism": f"replicas x{world}",
                            "l2": "flushed between timed steps (256 MB write)", "tiles": tiles},
+                # per step: the image up; the gradient, the objective scalars
+                # (3 totals + 3 per image, FP64) and the 4-byte status word down
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(img.numel() * 4),
-                        "d2h_bytes_per_step": int(img.numel() * 4 + 24)},
+                        "d2h_bytes_per_step": int(img.numel() * 4 + (3 + 3 * ctx.n_images) * 8 + 4)},
                 "gpu_launches": launches,
                 "roofline": roof, "kernels": kernels,
                 "clocks": clk.summary(), "cpu_baseline": cpu, "solve": solve, "gridded_forward": gridded,

@@ -85,6 +85,10 @@ struct mem_ctx {
     float* partial = nullptr;  // adjoint unit partials (FP32, one BLK x BLK block each)
     int* dstatus = nullptr;
     float* stage = nullptr;  // host-call staging (image, gradient)
+    // pinned host words for the scalar and status readback (one copy pair and
+    // one stream synchronisation per call; nullptr: pageable fallback)
+    double* hscal = nullptr;
+    size_t hscal_n = 0;
 
     // CUDA graphs: each repeated launch sequence is captured once (on a private
     // stream: the legacy default stream cannot be captured) and replayed on st
@@ -585,9 +589,27 @@ mem_status graphed(mem_ctx* c, mem_ctx::GraphSlot& g, const void* k1, const void
 
 mem_status read_scalars(mem_ctx* c, std::vector<double>& out) {
     out.resize(3 + 3 * (size_t)c->n_images);
-    CK(cudaMemcpyAsync(out.data(), c->scal, out.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st),
-       "scalar readback");
-    TRY(check_status(c));
+    const size_t n = out.size();
+    if (c->hscal_n < n + 1) {  // the scalars, then the status word
+        if (c->hscal) cudaFreeHost(c->hscal);
+        c->hscal = nullptr;
+        c->hscal_n = 0;
+        if (cudaMallocHost((void**)&c->hscal, (n + 1) * sizeof(double)) == cudaSuccess) c->hscal_n = n + 1;
+        else cudaGetLastError();  // pageable fallback below
+    }
+    if (c->hscal) {
+        // both words in pinned memory: two asynchronous copies, one synchronisation
+        int* hs = (int*)(c->hscal + n);
+        CK(cudaMemcpyAsync(c->hscal, c->scal, n * sizeof(double), cudaMemcpyDeviceToHost, c->st), "scalar readback");
+        CK(cudaMemcpyAsync(hs, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st), "status readback");
+        CK(cudaStreamSynchronize(c->st), "stream synchronize");
+        if (*hs & DEV_TIMEOUT) TRY(check_status(c));
+        std::copy(c->hscal, c->hscal + n, out.begin());
+    } else {
+        CK(cudaMemcpyAsync(out.data(), c->scal, n * sizeof(double), cudaMemcpyDeviceToHost, c->st),
+           "scalar readback");
+        TRY(check_status(c));
+    }
     for (double x : out)
         if (!std::isfinite(x)) return fail(c, MEM_ENUMERIC, "objective is not finite (pixels <= 0?)");
     return MEM_OK;
@@ -1188,6 +1210,7 @@ void mem_destroy(mem_ctx* c) {
     }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
+    if (c->hscal) cudaFreeHost(c->hscal);
     delete c;
 }
 
