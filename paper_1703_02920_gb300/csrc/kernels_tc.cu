@@ -97,18 +97,24 @@ __device__ __noinline__ void adj_drain(uint32_t tmem, float* out, int BLK, int n
         const uint32_t lb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * BLK);
         // column m of this lane's row: base[m * RB], coalesced over the warp
         float* base = out + (row_ok ? adj_partial_index(nrow, 0, BLK) : 0);
-        // per 16-column chunk: the TMEM load and the previous partial's loads
-        // are in flight together
+        // one TMEM wait per 16-column chunk; the unit's first drain stores,
+        // later ones add in place with reductions that return nothing, so the
+        // drain never waits for a load of the partial (each element is added
+        // to by one thread, in program order: the sum keeps its fixed order;
+        // the reduction flushes subnormal values, far below any gradient
+        // scale, to zero)
         for (int q = 0; q < BLK / 16; ++q) {
             uint32_t r[16];
             tmem_ld16(lb + q * 16, r);
-            float o[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) o[k] = (first || !row_ok) ? 0.f : base[(int64_t)(q * 16 + k) * RB];
             tmem_ld_wait(r);
             if (row_ok) {
+                if (first) {
 #pragma unroll
-                for (int k = 0; k < 16; ++k) base[(int64_t)(q * 16 + k) * RB] = o[k] + __uint_as_float(r[k]);
+                    for (int k = 0; k < 16; ++k) base[(int64_t)(q * 16 + k) * RB] = __uint_as_float(r[k]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) atomicAdd(base + (int64_t)(q * 16 + k) * RB, __uint_as_float(r[k]));
+                }
             }
         }
     }
