@@ -118,11 +118,10 @@ __global__ void __launch_bounds__(256) k_colsum(DevData d, ImgSrc src, double* _
         }
         psum[((int64_t)c * COL_RB + rb) * N + m] = t;
         pmax[((int64_t)c * COL_RB + rb) * N + m] = mx;
+        __threadfence();  // each writer's partials visible device-wide before the count below
     }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&count[c], 1u) == gridDim.x * gridDim.y - 1;
-    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&count[c], 1u) == gridDim.x * gridDim.y - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
