@@ -155,7 +155,10 @@ mem_status mem_objective_grad(mem_ctx *ctx, const float *image_dev, float *grad_
                               int32_t projected, double *out3_host);
 
 /* Same as mem_objective_grad with host buffers: copies image_host to the
- * device and grad_host back within the call (synchronous). */
+ * device and grad_host back within the call (synchronous: one stream
+ * synchronisation, which also reads the scalars and the status word back).
+ * Page-locked host buffers let both copies run asynchronously on the stream;
+ * pageable ones work too, through the driver's staging copies. */
 mem_status mem_objective_grad_host(mem_ctx *ctx, const float *image_host, float *grad_host,
                                    int32_t projected, double *out3_host);
 
