@@ -1,7 +1,7 @@
 // Tensor-core forward operator (Eq. 1 on the pixel grid) with the fused
 // per-visibility reduction, residual, weight and chi^2 partials.
 //
-//   T = Ey B^T  (tcgen05.mma kind::f16, 3-term split BF16, FP32 accumulation)
+//   T = Ey B^T  (tcgen05.mma kind::f16, 3-term FP16 or BF16 split, FP32 accumulation)
 //   V_k = sum_m Ex[k,m] T[k,m]
 //
 // The image operand is centred column by column, B'[n][m] = B[n][m] - c_m
@@ -15,9 +15,9 @@
 // 32 (j >> 4) + (j & 15) holds Re Ey[j,:] and the row 16 below it Im Ey[j,:]
 // (an order that keeps the producers' shared-memory stores free of bank
 // conflicts and each visibility's pair of rows in one warp's TMEM lanes), so
-// one M=128 MMA produces both the
-// real and the imaginary part of T for 64 visibilities, and one N <= 256
-// column block covers an N <= 256 image without regenerating Ey.  Two TMEM
+// one M=128 MMA produces both the real and the imaginary part of T for 64
+// visibilities, and one N <= 256 column block covers an N <= 256 image
+// without regenerating Ey.  Two TMEM
 // accumulators (2 x BN columns) let the epilogue of one tile overlap the MMAs
 // of the next.
 //
@@ -30,8 +30,8 @@
 // stays at the level of a 256-row image whatever N is.
 //
 // Roles (448 threads): warps 0-3 epilogue (TMEM lane = A row), warp 4 MMA
-// issue (one elected lane) + TMEM owner, warp 5 bulk copies of the image operand chunks,
-// warps 6-13 Ey producers.  Every mbarrier wait is bounded.
+// issue (one elected lane) + TMEM owner, warp 5 bulk copies of the image
+// operand chunks, warps 6-13 Ey producers.  Every mbarrier wait is bounded.
 #include <cstdint>
 
 #include "common.cuh"

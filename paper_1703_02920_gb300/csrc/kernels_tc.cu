@@ -9,7 +9,7 @@
 //   G[n,m] = sum_k Re(Ey)[k,n] Re(P)[k,m] + Im(Ey)[k,n] Im(P)[k,m],
 //   P[k,m] = y_k conj(Ex[k,m]),  y = w r.
 // Both contractions run on the 5th-generation tensor cores (tcgen05.mma,
-// kind::f16, accumulators in TMEM) in 3-term split BF16: x = hi + lo,
+// kind::f16, accumulators in TMEM) in a 3-term FP16 or BF16 split: x = hi + lo,
 // a b ~= a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32 accumulation.  The phase
 // tables are never stored: producer warps generate each tile in shared
 // memory from the exact fixed-point phases (one SFU sincos per 8 entries,
@@ -25,9 +25,6 @@
 
 namespace msk {
 
-// exp(-i 2 pi p) as (cos, -sin), p a fixed-point phase; SFU sincos of an angle
-// reduced exactly to [-pi, pi).
-
 // ===========================================================================
 // Adjoint: split-K over visibilities.  A CTA owns a contiguous run of
 // (channel, output block, visibility range) units, accumulates each unit's
@@ -38,7 +35,7 @@ namespace msk {
 // core-matrix row), the layout the per-visibility phase recurrences produce.
 // Roles: warp 4 MMA + TMEM owner; the other 13 warps produce operand stages,
 // and warps 0-3 (TMEM lane quadrants 0-3) also drain the accumulator to the
-// split-K partials at the end of each unit (once or twice per CTA).
+// split-K partials every ADJ_DRAIN stages and at the end of each unit.
 // ===========================================================================
 constexpr int ADJ_MAX_STAGES = 3;
 // Stages (of 16 visibilities) accumulated in TMEM before the accumulator is
@@ -46,7 +43,7 @@ constexpr int ADJ_MAX_STAGES = 3;
 // addition into its FP32 accumulator toward zero, so an accumulation of K
 // MMAs shrinks by up to ~K ulp; bounding K (6 MMAs per stage) bounds that
 // bias at ~2.5e-5 relative however many visibilities a unit spans.  The drains
-// add with ordinary round-to-nearest FP32 arithmetic, which has no such bias.
+// add with round-to-nearest FP32 reductions, which have no such bias.
 constexpr int ADJ_DRAIN = 256;
 constexpr int ADJ_THREADS = 448;
 constexpr int ADJ_PRODUCER_WARPS = ADJ_THREADS / 32 - 1;  // every warp but the MMA warp
