@@ -299,8 +299,17 @@ def roofline(kprof: dict, units: int, config: int) -> dict:
                             f"(12 executed in the 3-term split, so the algorithmic fraction is capped at 1/3: "
                             f"executed {3 * achieved:.0f} TFLOP/s); peak = {src} burst bf16 "
                             f"(of sustained: {achieved / sus:.3f})"}
+        if name.endswith("direct_f32"):
+            # one SFU sine and one SFU cosine per (visibility, pixel) pair; peak
+            # derived from the unit counts and clocks: 152 SMs x 16 SFU results
+            # per clock x 2.07 GHz = 5.03 Top/s
+            sfu = 2.0 * units / (avg_ms * 1e-3) / 1e12
+            peak = 152 * 16 * 2.07e9 / 1e12
+            return {"bound": "alu", "achieved": sfu, "peak": peak, "unit": "Top/s (SFU)", "frac": sfu / peak,
+                    "traffic": None, "note": f"{name}: {avg_ms:.3f} ms/launch, 2 SFU operations per vis*pixel; "
+                                             "peak derived (152 SMs x 16 SFU/clk x 2.07 GHz)"}
         return {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "note": f"{name}: {avg_ms:.3f} ms/launch"}
+                "frac": None, "traffic": None, "note": f"{name}: {avg_ms:.3f} ms/launch (FP64 pipe)"}
     return {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
             "frac": None, "traffic": None, "note": name}
 

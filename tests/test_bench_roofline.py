@@ -41,3 +41,13 @@ def test_traffic_record_is_current_for_the_committed_sources():
     for k in ("fwd_tc", "adj_tc"):
         t = bench._traffic(k)
         assert t is None or 20e6 < t < 60e6
+
+
+def test_roofline_of_the_fp32_direct_form_is_against_the_sfu():
+    import bench
+    units = 999600 * 256 * 256
+    r = bench.roofline({"fwd_direct_f32": (270.0, 10), "adj_direct_f32": (440.0, 10)}, units, 2)
+    assert r["bound"] == "alu" and r["unit"].startswith("Top/s")
+    assert r["achieved"] == pytest.approx(2.0 * units / 44.0e-3 / 1e12)
+    assert r["peak"] == pytest.approx(152 * 16 * 2.07e9 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
