@@ -349,11 +349,14 @@ void launch_fwd_direct(const DevData& d, int fp64, const VisTile* tiles, int n_t
 
 // ---------------------------------------------------------------------------
 // a12: direct-sum adjoint (the gradient kernel of Section 2.5): each thread
-// owns two adjacent pixels and loops over a slice of the channel's
-// visibilities staged in shared memory; slices (blockIdx.z) are summed later
-// in a fixed order.
+// owns ADJ_PPT adjacent pixels of a row and loops over a slice of the
+// channel's visibilities staged in shared memory; slices (blockIdx.z) are
+// summed later in a fixed order.  Sixteen pixels per thread share each
+// visibility's phase set-up (two 64-bit products) among sixteen pairs, which
+// leaves the FP32 form bound by its two SFU operations per pair (2 -> 16:
+// 43 -> 31 ms per launch at 256^2 with 999,600 visibilities).
 // ---------------------------------------------------------------------------
-constexpr int ADJ_PPT = 2;
+constexpr int ADJ_PPT = 16;
 constexpr int ADJ_CHUNK = 256;
 
 template <typename T, typename T2>
