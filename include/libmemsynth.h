@@ -122,9 +122,13 @@ mem_status mem_create(const mem_config *cfg, const double *u, const double *v,
                       const double *vis_obs, const double *sigma, const float *pb,
                       void *stream, mem_ctx **out);
 
+/* Waits for the context's stream, then frees everything the context owns:
+ * device buffers, CUDA graphs, events and its pinned host words.  The
+ * caller's stream is not destroyed.  NULL is ignored. */
 void mem_destroy(mem_ctx *ctx);
 
-/* Message for the last failing call on ctx (or a global one when ctx is NULL). */
+/* Message for the last failing call on ctx (or a global one when ctx is NULL);
+ * mem_status_string: a static name for a status code. */
 const char *mem_last_error(const mem_ctx *ctx);
 const char *mem_status_string(mem_status s);
 

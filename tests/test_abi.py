@@ -71,3 +71,21 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     with pytest.raises(ms.MemError) as e:
         ms.mem_create(96, 1e-6, 1e-6, offs, 0.0, 1e-4, 2, 0, u, v, vo, np.ones(3), np.ones((1, 96, 96), np.float32))
     assert e.value.status == 6   # tensor-core form shape
+
+
+def test_every_declaration_is_documented():
+    """Each function the header declares sits in a block (lines between blank
+    lines) that opens with its comment: the passage it implements, argument
+    layout, ownership, errors; one comment may cover a group of related
+    declarations."""
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        for block in re.split(r"\n\s*\n", src):
+            decl = re.search(r"^[A-Za-z_][A-Za-z0-9_ \*]*\b(mem_[a-z0-9_]+)\s*\(", block, flags=re.M)
+            if decl and not block.lstrip().startswith(("/*", "#", "typedef", "}")):
+                raise AssertionError((fn, decl.group(1)))
+            if decl and block.lstrip().startswith(("#", "typedef", "}")):
+                # a declaration inside a larger construct: its own comment must precede it
+                assert block[:decl.start()].rstrip().endswith("*/"), (fn, decl.group(1))
